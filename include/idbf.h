@@ -1,0 +1,201 @@
+/*
+ * idbf.h - C interface of the GB300 interpolative decomposition butterfly factorization.
+ *
+ * The library approximates a complementary low-rank N x N kernel matrix K(x_i, xi_j) by the
+ * product of L + 1 block-sparse factors (Pang, Ho and Yang, "Interpolative Decomposition
+ * Butterfly Factorization", Eq. 1):
+ *
+ *     K ~ U^L ... U^h S^h V^h ... V^L,   N = n0 2^L,
+ *
+ * built from (eps, k) interpolative decompositions of sampled blocks (Sec. 2.1) organised by
+ * leaf-root complementary skeletonization and recursive matrix splitting (Secs. 2.2-2.4), and
+ * applies it to blocks of vectors in O(N log N) (Sec. 1).
+ *
+ * Conventions shared by every call:
+ *   - All functions return an idbf_status; nothing throws across this interface.
+ *   - Vectors are caller-owned DEVICE memory on the plan's device: column-major blocks of
+ *     N rows and nrhs columns with leading dimension ld >= N, interleaved complex
+ *     (re, im). complex128 = two doubles, complex64 = two floats.
+ *   - Calls that take a `stream` (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream) are stream-ordered and return before the GPU work ends, except where stated.
+ *   - A plan is bound to the CUDA device that was current when it was created; calls on it
+ *     must be made with that device current. A plan is not thread-safe: calls on the same
+ *     plan from several host threads must be serialised by the caller.
+ *
+ * Factor layout (the "butterfly layout", shared by idbf_import_factors and idbf_save):
+ *   Level l = 0..L in apply order. Level l has m = 2^L nodes; node j reads segments 2j and
+ *   2j+1 of boundary l-1 (rows j*n0 .. j*n0+n0-1 of x when l = 0) and writes segments
+ *   (j / H) 2H + j % H + c H, c = 0, 1, of boundary l with H = 2^(L-l) (rows of y when
+ *   l = L). Boundary b = 0..L-1 holds 2m segments; seg_len[b][i] is the length of segment i.
+ *   Each node has two blocks c = 0, 1 holding a dense complex matrix M_c (rows x cols) and
+ *   index lists q_c, p_c. With u = concat(in_0, in_1) and t = concat(out_0, out_1):
+ *     levels l <  h_V (column IDs, V):   out_c = u[q_c] + M_c u[p_c],   |q_c| = rows, |p_c| = cols
+ *     level  l == h_V (middle factor S): out_c = M_c u
+ *     levels l >  h_V (row IDs, U):      t[q_c] += in_c,  t[p_c] += M_c in_c,
+ *                                        |q_c| = cols = |in_c|, |p_c| = rows
+ *   h_V = floor(L/2). On the U side M_c is the transpose T^T of the row ID's interpolation
+ *   block, so U = Lambda [I T]^T (Sec. 2.1, row ID); on the V side M_c = T of the column ID
+ *   V = [I T] Lambda^* (Sec. 2.1, Lemma 2.1).
+ */
+#ifndef IDBF_H
+#define IDBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct idbf_plan_s* idbf_plan;
+
+typedef enum {
+  IDBF_OK = 0,
+  IDBF_EINVAL = 1,       /* an argument is invalid (null pointer, size, mode); nothing was done */
+  IDBF_ENOMEM = 2,       /* device or host memory exhausted, or the planned bytes exceed free memory */
+  IDBF_ECUDA = 3,        /* a CUDA runtime call failed; idbf_last_cuda_error() names it */
+  IDBF_ERANKCAP = 4,     /* warning: some ID reached the rank parameter k (accuracy may exceed eps) */
+  IDBF_ETIMEOUT = 5,     /* a bounded device-side wait gave up; the results of the call are invalid */
+  IDBF_EFORMAT = 6,      /* factor arrays or a saved file are inconsistent */
+  IDBF_EUNSUPPORTED = 7  /* valid request this build does not handle (e.g. storage absent for a mode) */
+} idbf_status;
+
+/* ---- kernels (the numerical examples of Sec. 3) ---------------------------------------- */
+/* IDBF_KERNEL_FIO1D: K(x, xi) = exp(2 pi i (x xi + c(x) |xi|))   (Example 1, Eq. 1D-FIO)
+ *   c_profile 0: c(x) = (2 + sin(2 pi x) sin(4 pi x)) / 3
+ *   c_profile 1: c(x) = (2 + 0.2 sin(2 pi x)) / 16   (Example 1 as printed)
+ *   c_profile 2: c(x) = 0
+ * IDBF_KERNEL_DFT:   K(x, xi) = exp(sign 2 pi i x xi), sign = +1 or -1   (Example 3) */
+#define IDBF_KERNEL_FIO1D 0
+#define IDBF_KERNEL_DFT 1
+typedef struct {
+  int32_t kind;
+  int32_t sign;
+  int32_t c_profile;
+  int32_t reserved;
+} idbf_kernel;
+
+/* ---- construction parameters (Sec. 2.1 and Sec. 3) ------------------------------------- */
+#define IDBF_SAMPLE_MOCK_CHEBYSHEV 0 /* default; Sec. 2.1 */
+#define IDBF_SAMPLE_RANDOM 1         /* uniform without replacement, SplitMix64 stream per ID */
+#define IDBF_SAMPLE_ALL 2            /* no sampling (every candidate); exact-mode checks */
+
+/* storage formats of the factor entries on the device (bit i of a storage mask = format i) */
+#define IDBF_STORE_C128 0 /* complex FP64, 16 B per entry */
+#define IDBF_STORE_DF64 1 /* complex double-float: (re_hi, re_lo, im_hi, im_lo) floats, 16 B */
+#define IDBF_STORE_C64 2  /* complex FP32, 8 B per entry */
+
+typedef struct {
+  double eps;             /* ID tolerance (Eq. acc); k_eps = #leading |R_jj| > eps |R_11| */
+  double oversample;      /* t: t*k rows/columns sampled per ID (Eq. pivotedQR2); paper: 1 */
+  double oversample_leaf; /* t at the leaf step (k = n0 there); <= 0 means "same as t" */
+  int32_t leaf;           /* n0: points per leaf; N = n0 2^L with L >= 2 */
+  int32_t rank_cap;       /* k; 0 = min(#rows, #columns) of each block ("k = min{m,n}") */
+  int32_t sampling;       /* IDBF_SAMPLE_* */
+  int32_t storage;        /* IDBF_STORE_* format the factors are kept in after the build */
+  uint64_t seed;          /* random sampling stream seed */
+} idbf_params;
+
+/* Fill p with the defaults: eps 1e-6, t 1, t_leaf = t, n0 64, k = min dims, Mock-Chebyshev,
+ * C128 storage, seed 0. */
+void idbf_default_params(idbf_params* p);
+
+/* idbf_build - construct the IDBF of K on the point sets X = {x_i} and Omega = {xi_j}
+ * (Secs. 2.2-2.4) on the current device.
+ *   x_host, xi_host: N host doubles each, both sorted ascending (the dyadic trees of Sec. 1
+ *                    are taken over index ranges, leaf j = points j*n0 .. j*n0+n0-1).
+ *   The kernel entries are sampled and the per-node IDs computed by batched device kernels
+ *   (FP64 column-pivoted Householder QR, FP64 back-substitution). The call is synchronous on
+ *   `stream` (it returns when the plan is complete) and allocates device memory owned by the
+ *   returned plan. Returns IDBF_ERANKCAP (with a valid plan) when an ID hit rank_cap.
+ *   Errors: EINVAL (N not n0 2^L, L < 2, unsorted points, bad kernel/params), ENOMEM, ECUDA. */
+idbf_status idbf_build(const idbf_kernel* kernel, const double* x_host, const double* xi_host,
+                       int64_t N, const idbf_params* params, void* stream, idbf_plan* out);
+
+/* ---- import of host factors in the butterfly layout (used for oracle parity) ----------- */
+typedef struct {
+  int64_t N;
+  int32_t n0;
+  int32_t L;
+  const int32_t* seg_len;  /* [L][2m] segment lengths at boundaries 0..L-1 */
+  const int32_t* blk_rows; /* [L+1][m][2] rows of M_c */
+  const int32_t* blk_cols; /* [L+1][m][2] columns of M_c */
+  const int64_t* blk_moff; /* [L+1][m][2] offset of M_c in mat, in complex entries */
+  const int64_t* blk_ioff; /* [L+1][m][2] offset of q_c (then p_c) in idx */
+  const double* mat;       /* mat_len interleaved complex128 entries, each M_c row-major */
+  int64_t mat_len;
+  const int32_t* idx;      /* idx_len int32 indices */
+  int64_t idx_len;
+} idbf_host_factors;
+
+/* idbf_import_factors - copy factors given in host memory into a new plan stored in format
+ * `storage`. Every size and index is validated (EFORMAT on any inconsistency). Synchronous. */
+idbf_status idbf_import_factors(const idbf_host_factors* f, int32_t storage, void* stream,
+                                idbf_plan* out);
+
+/* ---- apply (Eq. 1) ---------------------------------------------------------------------- */
+#define IDBF_MODE_FP64 0   /* C128 storage, complex128 vectors, FP64 FMA */
+#define IDBF_MODE_DF64 1   /* DF64 storage, complex128 vectors, double-float (FP32 pair) arithmetic */
+#define IDBF_MODE_FP32 2   /* C64 storage, complex64 vectors, FP32 FMA */
+#define IDBF_MODE_TF32X3 3 /* C64 storage, complex64 vectors, 3xTF32 tensor-core block products */
+
+/* idbf_apply - y = K x for an N x nrhs block: x -> V levels -> S -> U levels -> y.
+ *   x, y: device pointers (may not alias), ld >= N, element type set by `mode` (above).
+ *   Uses a workspace owned by the plan; a call with a larger nrhs than any before allocates
+ *   it (cudaMalloc, synchronising), so reserve it with idbf_reserve before graph capture.
+ *   Errors: EINVAL, EUNSUPPORTED (storage for `mode` absent), ENOMEM, ECUDA. */
+idbf_status idbf_apply(idbf_plan plan, const void* x, void* y, int64_t nrhs, int64_t ld,
+                       int32_t mode, void* stream);
+
+/* idbf_apply_adjoint - y = K^* x: the factors in reverse order, each block conjugate-
+ * transposed (U-leaf^* first, V-leaf^* last). Same arguments and errors as idbf_apply. */
+idbf_status idbf_apply_adjoint(idbf_plan plan, const void* x, void* y, int64_t nrhs, int64_t ld,
+                               int32_t mode, void* stream);
+
+/* idbf_reserve - allocate the apply workspace for up to nrhs right-hand sides now. */
+idbf_status idbf_reserve(idbf_plan plan, int64_t nrhs);
+
+/* idbf_set_storage - keep exactly the formats in `mask` (bit IDBF_STORE_*). Missing formats
+ * are converted from a present one (C128 preferred as the source; C128 <-> DF64 in place when
+ * only one of them is kept). Stream-ordered; ENOMEM leaves the plan unchanged. */
+idbf_status idbf_set_storage(idbf_plan plan, uint32_t mask, void* stream);
+
+/* ---- statistics ------------------------------------------------------------------------- */
+#define IDBF_MAX_LEVELS 48
+typedef struct {
+  int64_t N;
+  int32_t n0, L, h_v, h_u;
+  uint32_t storage_mask;
+  int32_t rank_saturated;                  /* IDs that reached rank_cap during the build */
+  int64_t entries;                         /* stored factor entries (T and S blocks) */
+  int64_t index_entries;                   /* stored int32 skeleton/redundant indices */
+  int64_t level_entries[IDBF_MAX_LEVELS];  /* per level l = 0..L in apply order */
+  int32_t level_kmin[IDBF_MAX_LEVELS];     /* min / max output segment length of level l */
+  int32_t level_kmax[IDBF_MAX_LEVELS];
+  int64_t segment_entries;                 /* max over boundaries of the summed segment lengths */
+  double build_seconds;                    /* wall time of idbf_build (0 for imported plans) */
+  int64_t device_bytes;                    /* device memory held by the plan */
+} idbf_stats_t;
+
+/* idbf_stats - fill *s (host memory). Synchronous, no GPU work. */
+idbf_status idbf_stats(idbf_plan plan, idbf_stats_t* s);
+
+/* ---- checkpoint ------------------------------------------------------------------------- */
+/* idbf_save - write the factors (butterfly layout, complex128 entries) to a flat binary file
+ * with a versioned header. Requires C128 or DF64 storage. Synchronous.
+ * idbf_load - read such a file into a new plan stored as `storage`. EFORMAT on a bad file. */
+idbf_status idbf_save(idbf_plan plan, const char* path);
+idbf_status idbf_load(const char* path, int32_t storage, void* stream, idbf_plan* out);
+
+/* idbf_destroy - free the plan and all device memory it owns (NULL is a no-op). Synchronises
+ * the device first so that no queued work still reads the factors. */
+void idbf_destroy(idbf_plan plan);
+
+const char* idbf_strerror(idbf_status s);
+/* Name of the last CUDA error seen by this library on the calling thread ("" if none). */
+const char* idbf_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IDBF_H */

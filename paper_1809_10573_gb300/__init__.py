@@ -1,0 +1,193 @@
+"""GB300 interpolative decomposition butterfly factorization (IDBF).
+
+Python face of the C library in include/idbf.h: the construction (Secs. 2.1-2.4 of Pang, Ho and
+Yang), the apply y = K x through L + 1 block-sparse factors (Eq. 1) and its adjoint, with
+PyTorch used for device memory and streams. Every step of the apply runs in the library's CUDA
+kernels; this module only marshals arguments.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (KERNEL_DFT, KERNEL_FIO1D, MODE_DF64, MODE_FP32, MODE_FP64, MODE_TF32X3,
+                   SAMPLE_ALL, SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, STORE_C64, STORE_C128,
+                   STORE_DF64, IDBFError)
+
+__all__ = ["Plan", "IDBFError", "apply", "IDBFApply", "KERNEL_FIO1D", "KERNEL_DFT", "MODE_FP64",
+           "MODE_DF64", "MODE_FP32", "MODE_TF32X3", "STORE_C128", "STORE_DF64", "STORE_C64",
+           "SAMPLE_MOCK_CHEBYSHEV", "SAMPLE_RANDOM", "SAMPLE_ALL"]
+
+_VEC_DTYPE = {MODE_FP64: torch.complex128, MODE_DF64: torch.complex128,
+              MODE_FP32: torch.complex64, MODE_TF32X3: torch.complex64}
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _colmajor(x: torch.Tensor, N: int, dtype):
+    """(N,) or (N, R) -> an (R, N) contiguous tensor whose transpose is the column-major block."""
+    if x.dim() == 1:
+        x = x[:, None]
+    if x.shape[0] != N:
+        raise ValueError(f"expected {N} rows, got {x.shape[0]}")
+    if x.dtype != dtype:
+        raise TypeError(f"mode expects {dtype}, got {x.dtype}")
+    if not x.is_cuda:
+        raise ValueError("vectors must be CUDA tensors")
+    return x.t().contiguous()
+
+
+class Plan:
+    """A factorization resident on one GPU."""
+
+    def __init__(self, handle: int, device: int):
+        self._h = C.c_void_p(handle)
+        self.device = device
+        st = self.stats()
+        self.N, self.n0, self.L = st["N"], st["n0"], st["L"]
+
+    # ---- construction -------------------------------------------------------------------
+    @classmethod
+    def build(cls, x, xi, eps=1e-6, leaf=64, kernel="fio", c_profile=0, sign=-1, rank_cap=0,
+              oversample=1.0, oversample_leaf=0.0, sampling=SAMPLE_MOCK_CHEBYSHEV, seed=0,
+              storage=STORE_C128, stream=None):
+        L = _lib.lib()
+        k = _lib.Kernel(KERNEL_FIO1D if kernel == "fio" else KERNEL_DFT, sign, c_profile, 0)
+        p = _lib.Params()
+        L.idbf_default_params(C.byref(p))
+        p.eps, p.leaf, p.rank_cap, p.oversample, p.oversample_leaf = eps, leaf, rank_cap, oversample, oversample_leaf
+        p.sampling, p.seed, p.storage = sampling, seed, storage
+        xa = np.ascontiguousarray(x, dtype=np.float64)
+        xia = np.ascontiguousarray(xi, dtype=np.float64)
+        out = C.c_void_p()
+        st = L.idbf_build(C.byref(k), xa.ctypes.data, xia.ctypes.data, xa.size, C.byref(p),
+                          _stream_ptr(stream), C.byref(out))
+        _lib.check(st, "idbf_build")
+        plan = cls(out.value, torch.cuda.current_device())
+        plan.rank_capped = st == _lib.ERANKCAP
+        return plan
+
+    @classmethod
+    def import_factors(cls, ex: dict, storage=STORE_C128, stream=None):
+        """Import factors given in the butterfly layout (a dict of numpy arrays)."""
+        L = _lib.lib()
+        keep = dict(seg_len=np.ascontiguousarray(ex["seg_len"], dtype=np.int32),
+                    rows=np.ascontiguousarray(ex["blk_rows"], dtype=np.int32),
+                    cols=np.ascontiguousarray(ex["blk_cols"], dtype=np.int32),
+                    moff=np.ascontiguousarray(ex["blk_moff"], dtype=np.int64),
+                    ioff=np.ascontiguousarray(ex["blk_ioff"], dtype=np.int64),
+                    mat=np.ascontiguousarray(ex["mat"], dtype=np.complex128),
+                    idx=np.ascontiguousarray(ex["idx"], dtype=np.int32))
+        f = _lib.HostFactors(int(ex["N"]), int(ex["n0"]), int(ex["L"]), keep["seg_len"].ctypes.data,
+                             keep["rows"].ctypes.data, keep["cols"].ctypes.data, keep["moff"].ctypes.data,
+                             keep["ioff"].ctypes.data, keep["mat"].ctypes.data, keep["mat"].size,
+                             keep["idx"].ctypes.data, keep["idx"].size)
+        out = C.c_void_p()
+        _lib.check(L.idbf_import_factors(C.byref(f), storage, _stream_ptr(stream), C.byref(out)),
+                   "idbf_import_factors")
+        return cls(out.value, torch.cuda.current_device())
+
+    @classmethod
+    def load(cls, path: str, storage=STORE_C128, stream=None):
+        out = C.c_void_p()
+        _lib.check(_lib.lib().idbf_load(path.encode(), storage, _stream_ptr(stream), C.byref(out)), "idbf_load")
+        return cls(out.value, torch.cuda.current_device())
+
+    def save(self, path: str):
+        _lib.check(_lib.lib().idbf_save(self._h, path.encode()), "idbf_save")
+
+    # ---- apply --------------------------------------------------------------------------
+    def _run(self, fn, x, mode, out, stream):
+        dt = _VEC_DTYPE.get(mode, torch.complex128)  # unknown modes are rejected by the library
+        xt = _colmajor(x, self.N, dt)
+        R = xt.shape[0]
+        if out is None:
+            yt = torch.empty((R, self.N), dtype=dt, device=xt.device)
+        else:
+            yt = out.t() if out.dim() == 2 else out[None, :]
+            if not (yt.is_contiguous() and yt.shape == (R, self.N) and yt.dtype == dt):
+                raise ValueError("out must be a column-major (N, R) block of the mode's dtype")
+        _lib.check(fn(self._h, xt.data_ptr(), yt.data_ptr(), R, self.N, mode, _stream_ptr(stream)),
+                   fn.__name__)
+        if out is not None:
+            return out
+        return yt[0] if x.dim() == 1 else yt.t()
+
+    def apply(self, x, mode=MODE_FP64, out=None, stream=None):
+        """y = K x for x of shape (N,) or (N, R)."""
+        return self._run(_lib.lib().idbf_apply, x, mode, out, stream)
+
+    def apply_adjoint(self, x, mode=MODE_FP64, out=None, stream=None):
+        """y = K^* x."""
+        return self._run(_lib.lib().idbf_apply_adjoint, x, mode, out, stream)
+
+    def apply_raw(self, x_ptr, y_ptr, nrhs, ld, mode, stream_ptr, adjoint=False):
+        """The C call itself on raw device pointers (column-major blocks)."""
+        L = _lib.lib()
+        fn = L.idbf_apply_adjoint if adjoint else L.idbf_apply
+        return _lib.check(fn(self._h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), nrhs, ld, mode, C.c_void_p(stream_ptr)),
+                          fn.__name__)
+
+    def reserve(self, nrhs: int):
+        _lib.check(_lib.lib().idbf_reserve(self._h, nrhs), "idbf_reserve")
+
+    def set_storage(self, *formats, stream=None):
+        mask = 0
+        for f in formats:
+            mask |= 1 << f
+        _lib.check(_lib.lib().idbf_set_storage(self._h, mask, _stream_ptr(stream)), "idbf_set_storage")
+
+    def stats(self) -> dict:
+        s = _lib.Stats()
+        _lib.check(_lib.lib().idbf_stats(self._h, C.byref(s)), "idbf_stats")
+        nl = s.L + 1
+        return dict(N=s.N, n0=s.n0, L=s.L, h_v=s.h_v, h_u=s.h_u, storage_mask=s.storage_mask,
+                    rank_saturated=s.rank_saturated, entries=s.entries, index_entries=s.index_entries,
+                    level_entries=list(s.level_entries[:nl]), level_kmin=list(s.level_kmin[:nl]),
+                    level_kmax=list(s.level_kmax[:nl]), segment_entries=s.segment_entries,
+                    build_seconds=s.build_seconds, device_bytes=s.device_bytes)
+
+    def algorithmic_bytes(self, nrhs: int = 1, entry_bytes: int = 16, vec_bytes: int = 16) -> int:
+        """Bytes one apply must move at least: every stored factor entry once, the int32
+        skeleton / redundant indices once, x read and y written."""
+        st = self.stats()
+        return st["entries"] * entry_bytes + st["index_entries"] * 4 + 2 * self.N * nrhs * vec_bytes
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.lib().idbf_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def apply(plan: Plan, x, mode=MODE_FP64):
+    """Differentiable y = K x (see IDBFApply)."""
+    return IDBFApply.apply(x, plan, mode)
+
+
+class IDBFApply(torch.autograd.Function):
+    """y = K x with the hand-written adjoint as backward.
+
+    PyTorch's complex autograd passes grad_y = dL/d(conj y) and expects dL/d(conj x); for the
+    linear map y = K x that is grad_x = K^* grad_y, the conjugate-transpose butterfly (factors in
+    reverse order, each block conjugate-transposed)."""
+
+    @staticmethod
+    def forward(ctx, x, plan, mode):
+        ctx.plan, ctx.mode = plan, mode
+        return plan.apply(x.detach(), mode=mode)
+
+    @staticmethod
+    def backward(ctx, gy):
+        return ctx.plan.apply_adjoint(gy.contiguous(), mode=ctx.mode), None, None

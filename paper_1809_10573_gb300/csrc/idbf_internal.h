@@ -1,0 +1,111 @@
+// Internal structures of the IDBF library (not part of the C interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "idbf.h"
+
+namespace idbf {
+
+// Level kinds of the butterfly layout (apply order).
+enum LevelKind { KIND_V = 0, KIND_S = 1, KIND_U = 2 };
+
+// Everything a level kernel needs, passed by value.
+struct DevLevel {
+  int kind;
+  int lev;
+  int L;
+  int H;   // 2^(L - lev): output c of node j is segment (j / H) 2H + j % H + c H
+  int m;
+  int n0;
+  const int32_t* rows;    // [m][2]
+  const int32_t* cols;    // [m][2]
+  const int64_t* moff;    // [m][2] entry offset of M_c (column-major: M(r, j) at j*rows + r)
+  const int64_t* ioff;    // [m][2] offset of the index lists in idx
+  const int32_t* idx;
+  const int64_t* in_off;  // boundary lev-1 segment offsets (nullptr at lev 0)
+  const int32_t* in_len;
+  const int64_t* out_off; // boundary lev segment offsets (nullptr at lev L)
+  const int32_t* out_len;
+};
+
+struct LevelInfo {
+  int kind = 0;
+  int64_t entries = 0;
+  int64_t idx_entries = 0;
+  int max_rows = 0;      // max rows of one block
+  int max_cols = 0;      // max cols of one block
+  int max_in = 0;        // max summed input length of a node
+  int max_out = 0;       // max summed output length of a node
+  int max_rows_pair = 0; // max rows_0 + rows_1 of a node
+  int max_cols_pair = 0; // max cols_0 + cols_1 of a node
+  int kmin = 0, kmax = 0;  // output segment lengths
+};
+
+struct Plan {
+  int device = 0;
+  int64_t N = 0;
+  int n0 = 0, L = 0, m = 0, hV = 0, hU = 0;
+  std::vector<LevelInfo> lv;           // L + 1
+  // host copy of the structure
+  std::vector<int32_t> h_rows, h_cols;  // [(L+1) m 2]
+  std::vector<int64_t> h_moff, h_ioff;
+  std::vector<int32_t> h_seg_len;       // [L][2m]
+  std::vector<int64_t> h_seg_off;       // [L][2m]
+  std::vector<int64_t> seg_total;       // [L]
+  int64_t max_seg_total = 0;
+  int64_t mat_len = 0;                  // entries
+  int64_t idx_len = 0;
+  // device
+  void* d_meta = nullptr;
+  int32_t* d_rows = nullptr;
+  int32_t* d_cols = nullptr;
+  int64_t* d_moff = nullptr;
+  int64_t* d_ioff = nullptr;
+  int32_t* d_seg_len = nullptr;
+  int64_t* d_seg_off = nullptr;
+  int32_t* d_idx = nullptr;
+  void* d_mat[3] = {nullptr, nullptr, nullptr};
+  void* d_ws = nullptr;
+  size_t ws_bytes = 0;
+  int rank_saturated = 0;
+  double build_seconds = 0.0;
+
+  DevLevel level(int l) const;
+  size_t device_bytes() const;
+};
+
+// error bookkeeping (thread-local last CUDA error name)
+void set_cuda_error(cudaError_t e);
+#define IDBF_CUDA_TRY(call)                       \
+  do {                                            \
+    cudaError_t _e = (call);                      \
+    if (_e != cudaSuccess) {                      \
+      ::idbf::set_cuda_error(_e);                 \
+      return _e == cudaErrorMemoryAllocation ? IDBF_ENOMEM : IDBF_ECUDA; \
+    }                                             \
+  } while (0)
+
+// Build the device-side structure of a plan whose host structure (h_*) is filled in and whose
+// matrices are given column-major per block in `mat_c128` (host, interleaved) or already on the
+// device (`dev_mat_c128`, ownership passes to the plan). Computes level infos and segment offsets.
+idbf_status finalize_structure(Plan* p);
+idbf_status upload_structure(Plan* p, const int32_t* idx_host, cudaStream_t st);
+
+// storage conversion kernels (plan.cu)
+idbf_status convert_storage(Plan* p, uint32_t mask, cudaStream_t st);
+
+// workspace (apply.cu)
+idbf_status ensure_workspace(Plan* p, int64_t nrhs);
+
+inline int64_t boundary_index(int b, int64_t m) { return (int64_t)b * 2 * m; }
+
+}  // namespace idbf
+
+struct idbf_plan_s {
+  idbf::Plan p;
+};

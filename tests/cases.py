@@ -1,0 +1,35 @@
+"""Seeded parity cases: oracle factorizations of the paper's workloads at sizes the oracle
+builds in seconds (several nodes per level, ragged segment lengths, odd and even L)."""
+import functools
+
+import numpy as np
+
+from oracle import idbf, kernels
+from paper_1809_10573_gb300 import inputs
+
+CASES = {
+    # name: (N, n0, kernel, grid, eps, build kwargs)
+    "dft_1024": (1024, 16, ("dft", -1, 0), "uniform", 1e-8, {}),
+    "dft_jit_2048_oddL": (2048, 16, ("dft", -1, 0), "jitter", 1e-6, {}),            # L = 7
+    "fio_base_4096": (4096, 64, ("fio", 0, 0), "uniform", 1e-8, dict(t=2, t_leaf=4)),  # config 1
+    "fio_paper_2048": (2048, 8, ("fio", 0, 1), "uniform", 1e-6, {}),                # Example 1, L = 8
+    "fio_base_8192_oddL": (8192, 64, ("fio", 0, 0), "uniform", 1e-6, dict(t=2, t_leaf=4)),  # L = 7
+}
+
+
+def kernel_of(spec):
+    kind, sign, prof = spec
+    return kernels.Kernel(kernels.KIND_FIO if kind == "fio" else kernels.KIND_DFT, sign=sign, c_profile=prof)
+
+
+def grid_of(name, N):
+    return inputs.uniform_grid(N) if CASES[name][3] == "uniform" else inputs.jittered_grid(N, seed=N)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_case(name):
+    N, n0, kspec, _, eps, kw = CASES[name]
+    x, xi = grid_of(name, N)
+    K = kernel_of(kspec)
+    F = idbf.build(K, x, xi, eps, n0, **kw)
+    return dict(N=N, n0=n0, x=x, xi=xi, K=K, F=F, ex=idbf.export(F), eps=eps)
