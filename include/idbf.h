@@ -54,7 +54,7 @@ typedef enum {
   IDBF_EINVAL = 1,       /* an argument is invalid (null pointer, size, mode); nothing was done */
   IDBF_ENOMEM = 2,       /* device or host memory exhausted, or the planned bytes exceed free memory */
   IDBF_ECUDA = 3,        /* a CUDA runtime call failed; idbf_last_cuda_error() names it */
-  IDBF_ERANKCAP = 4,     /* warning: some ID reached the rank parameter k (accuracy may exceed eps) */
+  IDBF_ERANKCAP = 4,     /* warning: some ID stopped at its maximum rank min(k, samples) with columns left (accuracy may exceed eps) */
   IDBF_ETIMEOUT = 5,     /* a bounded device-side wait gave up; the results of the call are invalid */
   IDBF_EFORMAT = 6,      /* factor arrays or a saved file are inconsistent */
   IDBF_EUNSUPPORTED = 7  /* valid request this build does not handle (e.g. storage absent for a mode) */
@@ -166,7 +166,7 @@ typedef struct {
   int64_t N;
   int32_t n0, L, h_v, h_u;
   uint32_t storage_mask;
-  int32_t rank_saturated;                  /* IDs that reached rank_cap during the build */
+  int32_t rank_saturated;                  /* IDs that stopped at their maximum rank, not by eps */
   int64_t entries;                         /* stored factor entries (T and S blocks) */
   int64_t index_entries;                   /* stored int32 skeleton/redundant indices */
   int64_t level_entries[IDBF_MAX_LEVELS];  /* per level l = 0..L in apply order */

@@ -492,7 +492,6 @@ template <class P, int RB>
 static idbf_status run_levels(Plan* p, const void* x, void* y, int64_t R, int64_t ld, bool adjoint, cudaStream_t st,
                               int fmt) {
   using V = typename P::vec_t;
-  const typename P::mat_t* mat = (const typename P::mat_t*)p->d_mat[fmt];
   V* ws0 = (V*)p->d_ws;
   V* ws1 = (V*)((char*)p->d_ws + (size_t)p->max_seg_total * R * 16);
   const int nlev = p->L + 1;
@@ -500,6 +499,7 @@ static idbf_status run_levels(Plan* p, const void* x, void* y, int64_t R, int64_
     const int l = adjoint ? p->L - step : step;
     const LevelInfo& li = p->lv[l];
     const DevLevel d = p->level(l);
+    const typename P::mat_t* mat = (const typename P::mat_t*)p->lmat[fmt][l];
     IO<V> io;
     io.x = (const V*)x; io.ldx = ld; io.y = (V*)y; io.ldy = ld; io.R = (int)R;
     // boundary b lives in buffer b % 2; forward level l reads b = l-1 and writes b = l,
@@ -550,7 +550,7 @@ static idbf_status apply_common(idbf_plan h, const void* x, void* y, int64_t nrh
     case IDBF_MODE_FP32: fmt = IDBF_STORE_C64; break;
     default: return mode == IDBF_MODE_TF32X3 ? IDBF_EUNSUPPORTED : IDBF_EINVAL;
   }
-  if (p->mat_len > 0 && !p->d_mat[fmt]) return IDBF_EUNSUPPORTED;
+  if (!p->has_format(fmt)) return IDBF_EUNSUPPORTED;
   idbf_status s = ensure_workspace(p, nrhs);
   if (s != IDBF_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;

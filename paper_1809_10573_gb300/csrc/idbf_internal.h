@@ -58,9 +58,10 @@ struct Plan {
   std::vector<int64_t> h_seg_off;       // [L][2m]
   std::vector<int64_t> seg_total;       // [L]
   int64_t max_seg_total = 0;
-  int64_t mat_len = 0;                  // entries
-  int64_t idx_len = 0;
-  // device
+  int64_t mat_len = 0;                  // entries over all levels
+  int64_t idx_len = 0;                  // indices over all levels
+  // device: one matrix arena per level and format (offsets moff are relative to the level),
+  // one index array per level (ioff relative to the level)
   void* d_meta = nullptr;
   int32_t* d_rows = nullptr;
   int32_t* d_cols = nullptr;
@@ -68,8 +69,10 @@ struct Plan {
   int64_t* d_ioff = nullptr;
   int32_t* d_seg_len = nullptr;
   int64_t* d_seg_off = nullptr;
-  int32_t* d_idx = nullptr;
-  void* d_mat[3] = {nullptr, nullptr, nullptr};
+  std::vector<int64_t> lmat_len;        // [L+1] entries
+  std::vector<int64_t> lidx_len;        // [L+1]
+  std::vector<void*> lmat[3];           // [format][L+1]
+  std::vector<int32_t*> lidx;           // [L+1]
   void* d_ws = nullptr;
   size_t ws_bytes = 0;
   int rank_saturated = 0;
@@ -77,6 +80,8 @@ struct Plan {
 
   DevLevel level(int l) const;
   size_t device_bytes() const;
+  bool has_format(int f) const;         // every non-empty level holds format f
+  void init_levels();                   // size the per-level vectors (L set)
 };
 
 // error bookkeeping (thread-local last CUDA error name)
@@ -90,11 +95,10 @@ void set_cuda_error(cudaError_t e);
     }                                             \
   } while (0)
 
-// Build the device-side structure of a plan whose host structure (h_*) is filled in and whose
-// matrices are given column-major per block in `mat_c128` (host, interleaved) or already on the
-// device (`dev_mat_c128`, ownership passes to the plan). Computes level infos and segment offsets.
+// Level infos and segment offsets from the host structure (h_rows, h_cols, h_seg_len).
 idbf_status finalize_structure(Plan* p);
-idbf_status upload_structure(Plan* p, const int32_t* idx_host, cudaStream_t st);
+// Copy the host structure (block shapes and offsets, segment lengths and offsets) to the device.
+idbf_status upload_structure(Plan* p, cudaStream_t st);
 
 // storage conversion kernels (plan.cu)
 idbf_status convert_storage(Plan* p, uint32_t mask, cudaStream_t st);

@@ -37,7 +37,7 @@ DevLevel Plan::level(int l) const {
   d.cols = d_cols + l * nb;
   d.moff = d_moff + l * nb;
   d.ioff = d_ioff + l * nb;
-  d.idx = d_idx;
+  d.idx = lidx[l];
   d.in_off = l > 0 ? d_seg_off + (l - 1) * nb : nullptr;
   d.in_len = l > 0 ? d_seg_len + (l - 1) * nb : nullptr;
   d.out_off = l < L ? d_seg_off + l * nb : nullptr;
@@ -52,8 +52,22 @@ size_t Plan::device_bytes() const {
   b += (size_t)L * 2 * m * (sizeof(int32_t) + sizeof(int64_t));
   b += idx_len * sizeof(int32_t);
   for (int f = 0; f < 3; ++f)
-    if (d_mat[f]) b += mat_len * (f == IDBF_STORE_C64 ? 8 : 16);
+    for (int l = 0; l <= L && l < (int)lmat[f].size(); ++l)
+      if (lmat[f][l]) b += lmat_len[l] * (f == IDBF_STORE_C64 ? 8 : 16);
   return b;
+}
+
+bool Plan::has_format(int f) const {
+  for (int l = 0; l <= L; ++l)
+    if (lmat_len[l] > 0 && !lmat[f][l]) return false;
+  return true;
+}
+
+void Plan::init_levels() {
+  lmat_len.assign(L + 1, 0);
+  lidx_len.assign(L + 1, 0);
+  for (int f = 0; f < 3; ++f) lmat[f].assign(L + 1, nullptr);
+  lidx.assign(L + 1, nullptr);
 }
 
 idbf_status finalize_structure(Plan* p) {
@@ -108,7 +122,7 @@ idbf_status finalize_structure(Plan* p) {
   return IDBF_OK;
 }
 
-idbf_status upload_structure(Plan* p, const int32_t* idx_host, cudaStream_t st) {
+idbf_status upload_structure(Plan* p, cudaStream_t st) {
   const int64_t nb = (int64_t)(p->L + 1) * p->m * 2;
   const int64_t ns = (int64_t)p->L * 2 * p->m;
   size_t bytes = nb * (2 * sizeof(int32_t) + 2 * sizeof(int64_t)) + ns * (sizeof(int32_t) + sizeof(int64_t));
@@ -126,10 +140,6 @@ idbf_status upload_structure(Plan* p, const int32_t* idx_host, cudaStream_t st) 
   IDBF_CUDA_TRY(cudaMemcpyAsync(p->d_rows, p->h_rows.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   IDBF_CUDA_TRY(cudaMemcpyAsync(p->d_cols, p->h_cols.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   IDBF_CUDA_TRY(cudaMemcpyAsync(p->d_seg_len, p->h_seg_len.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-  if (idx_host && p->idx_len > 0) {
-    IDBF_CUDA_TRY(cudaMalloc(&p->d_idx, p->idx_len * sizeof(int32_t)));
-    IDBF_CUDA_TRY(cudaMemcpyAsync(p->d_idx, idx_host, p->idx_len * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-  }
   return IDBF_OK;
 }
 
@@ -184,50 +194,59 @@ static int conv_grid(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
 }
 
-idbf_status convert_storage(Plan* p, uint32_t mask, cudaStream_t st) {
-  const int64_t n = p->mat_len;
-  const bool has128 = p->d_mat[IDBF_STORE_C128], hasdf = p->d_mat[IDBF_STORE_DF64];
-  if (!has128 && !hasdf) return IDBF_EUNSUPPORTED;  // C64 alone cannot be widened
+static idbf_status convert_level(Plan* p, int l, uint32_t mask, cudaStream_t st) {
+  const int64_t n = p->lmat_len[l];
+  void** m = nullptr;
+  void* mm[3] = {p->lmat[0][l], p->lmat[1][l], p->lmat[2][l]};
+  m = mm;
+  const bool has128 = m[IDBF_STORE_C128], hasdf = m[IDBF_STORE_DF64];
   const bool want128 = mask & (1u << IDBF_STORE_C128), wantdf = mask & (1u << IDBF_STORE_DF64),
              want64 = mask & (1u << IDBF_STORE_C64);
-  if (n == 0) {
-    for (int f = 0; f < 3; ++f)
-      if (!(mask & (1u << f)) && p->d_mat[f]) { cudaFree(p->d_mat[f]); p->d_mat[f] = nullptr; }
-    return IDBF_OK;
-  }
-  const int g = conv_grid(n);
-  // C64 from the wide format first (needs the wide copy still present)
-  if (want64 && !p->d_mat[IDBF_STORE_C64]) {
-    void* d = nullptr;
-    IDBF_CUDA_TRY(cudaMalloc(&d, n * sizeof(float2)));
-    if (has128) k_c128_to_c64<<<g, 256, 0, st>>>((const double2*)p->d_mat[IDBF_STORE_C128], (float2*)d, n);
-    else k_df64_to_c64<<<g, 256, 0, st>>>((const float4*)p->d_mat[IDBF_STORE_DF64], (float2*)d, n);
-    IDBF_CUDA_TRY(cudaGetLastError());
-    p->d_mat[IDBF_STORE_C64] = d;
-  }
-  if (want128 && wantdf && !(has128 && hasdf)) {
-    void* d = nullptr;
-    IDBF_CUDA_TRY(cudaMalloc(&d, n * 16));
-    if (has128) { k_c128_to_df64<<<g, 256, 0, st>>>((const double2*)p->d_mat[IDBF_STORE_C128], (float4*)d, n); p->d_mat[IDBF_STORE_DF64] = d; }
-    else { k_df64_to_c128<<<g, 256, 0, st>>>((const float4*)p->d_mat[IDBF_STORE_DF64], (double2*)d, n); p->d_mat[IDBF_STORE_C128] = d; }
-    IDBF_CUDA_TRY(cudaGetLastError());
-  } else if (want128 && !has128) {  // only DF64 present: convert in place
-    k_df64_to_c128_inplace<<<g, 256, 0, st>>>(p->d_mat[IDBF_STORE_DF64], n);
-    IDBF_CUDA_TRY(cudaGetLastError());
-    p->d_mat[IDBF_STORE_C128] = p->d_mat[IDBF_STORE_DF64];
-    p->d_mat[IDBF_STORE_DF64] = nullptr;
-  } else if (wantdf && !hasdf) {  // only C128 present: convert in place
-    k_c128_to_df64_inplace<<<g, 256, 0, st>>>(p->d_mat[IDBF_STORE_C128], n);
-    IDBF_CUDA_TRY(cudaGetLastError());
-    p->d_mat[IDBF_STORE_DF64] = p->d_mat[IDBF_STORE_C128];
-    p->d_mat[IDBF_STORE_C128] = nullptr;
-  }
-  IDBF_CUDA_TRY(cudaStreamSynchronize(st));
-  for (int f = 0; f < 3; ++f)
-    if (!(mask & (1u << f)) && p->d_mat[f]) {
-      IDBF_CUDA_TRY(cudaFree(p->d_mat[f]));
-      p->d_mat[f] = nullptr;
+  if (n > 0) {
+    if (!has128 && !hasdf) return IDBF_EUNSUPPORTED;  // C64 alone cannot be widened
+    const int g = conv_grid(n);
+    if (want64 && !m[IDBF_STORE_C64]) {
+      void* d = nullptr;
+      IDBF_CUDA_TRY(cudaMalloc(&d, n * sizeof(float2)));
+      if (has128) k_c128_to_c64<<<g, 256, 0, st>>>((const double2*)m[IDBF_STORE_C128], (float2*)d, n);
+      else k_df64_to_c64<<<g, 256, 0, st>>>((const float4*)m[IDBF_STORE_DF64], (float2*)d, n);
+      IDBF_CUDA_TRY(cudaGetLastError());
+      m[IDBF_STORE_C64] = d;
     }
+    if (want128 && wantdf && !(has128 && hasdf)) {
+      void* d = nullptr;
+      IDBF_CUDA_TRY(cudaMalloc(&d, n * 16));
+      if (has128) { k_c128_to_df64<<<g, 256, 0, st>>>((const double2*)m[IDBF_STORE_C128], (float4*)d, n); m[IDBF_STORE_DF64] = d; }
+      else { k_df64_to_c128<<<g, 256, 0, st>>>((const float4*)m[IDBF_STORE_DF64], (double2*)d, n); m[IDBF_STORE_C128] = d; }
+      IDBF_CUDA_TRY(cudaGetLastError());
+    } else if (want128 && !has128) {  // only DF64 present: convert in place
+      k_df64_to_c128_inplace<<<g, 256, 0, st>>>(m[IDBF_STORE_DF64], n);
+      IDBF_CUDA_TRY(cudaGetLastError());
+      m[IDBF_STORE_C128] = m[IDBF_STORE_DF64];
+      m[IDBF_STORE_DF64] = nullptr;
+    } else if (wantdf && !hasdf) {  // only C128 present: convert in place
+      k_c128_to_df64_inplace<<<g, 256, 0, st>>>(m[IDBF_STORE_C128], n);
+      IDBF_CUDA_TRY(cudaGetLastError());
+      m[IDBF_STORE_DF64] = m[IDBF_STORE_C128];
+      m[IDBF_STORE_C128] = nullptr;
+    }
+    IDBF_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  for (int f = 0; f < 3; ++f) {
+    if (!(mask & (1u << f)) && m[f]) {
+      IDBF_CUDA_TRY(cudaFree(m[f]));
+      m[f] = nullptr;
+    }
+    p->lmat[f][l] = m[f];
+  }
+  return IDBF_OK;
+}
+
+idbf_status convert_storage(Plan* p, uint32_t mask, cudaStream_t st) {
+  for (int l = 0; l <= p->L; ++l) {
+    idbf_status s = convert_level(p, l, mask, st);
+    if (s != IDBF_OK) return s;
+  }
   return IDBF_OK;
 }
 
@@ -327,39 +346,57 @@ idbf_status idbf_import_factors(const idbf_host_factors* f, int32_t storage, voi
   Plan& p = h->p;
   cudaGetDevice(&p.device);
   p.N = f->N; p.n0 = f->n0; p.L = f->L; p.m = 1 << f->L; p.hV = f->L / 2; p.hU = f->L - p.hV;
-  const int64_t nb = (int64_t)(p.L + 1) * p.m * 2;
+  p.init_levels();
+  const int64_t nb = (int64_t)(p.L + 1) * p.m * 2, nbl = (int64_t)p.m * 2;
   p.h_rows.assign(f->blk_rows, f->blk_rows + nb);
   p.h_cols.assign(f->blk_cols, f->blk_cols + nb);
-  p.h_ioff.assign(f->blk_ioff, f->blk_ioff + nb);
   p.h_seg_len.assign(f->seg_len, f->seg_len + (int64_t)p.L * 2 * p.m);
-  // compact, column-major device copy of the matrices (the host blocks are row-major)
   p.h_moff.resize(nb);
-  int64_t tot = 0;
-  for (int64_t o = 0; o < nb; ++o) { p.h_moff[o] = tot; tot += (int64_t)p.h_rows[o] * p.h_cols[o]; }
-  p.mat_len = tot;
-  p.idx_len = f->idx_len;
+  p.h_ioff.resize(nb);
   finalize_structure(&p);
-  std::vector<double> colmajor;
-  try { colmajor.resize(2 * (size_t)tot); } catch (...) { delete h; return IDBF_ENOMEM; }
-  for (int64_t o = 0; o < nb; ++o) {
-    const int64_t r = p.h_rows[o], c = p.h_cols[o];
-    const double* src = f->mat + 2 * f->blk_moff[o];
-    double* dst = colmajor.data() + 2 * p.h_moff[o];
-    for (int64_t i = 0; i < r; ++i)
-      for (int64_t j = 0; j < c; ++j) {
-        dst[2 * (j * r + i)] = src[2 * (i * c + j)];
-        dst[2 * (j * r + i) + 1] = src[2 * (i * c + j) + 1];
-      }
-  }
-  s = upload_structure(&p, f->idx, st);
-  if (s == IDBF_OK && tot > 0) {
-    cudaError_t e = cudaMalloc(&p.d_mat[IDBF_STORE_C128], tot * 16);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p.d_mat[IDBF_STORE_C128], colmajor.data(), tot * 16, cudaMemcpyHostToDevice, st);
+  // per level: compact column-major copy of the blocks (the host blocks are row-major) and the
+  // level's index lists (q_c then p_c per block)
+  for (int l = 0; l <= p.L && s == IDBF_OK; ++l) {
+    int64_t tot = 0, itot = 0;
+    for (int64_t o = l * nbl; o < (l + 1) * nbl; ++o) {
+      p.h_moff[o] = tot;
+      tot += (int64_t)p.h_rows[o] * p.h_cols[o];
+      p.h_ioff[o] = itot;
+      if (p.lv[l].kind != KIND_S) itot += p.h_rows[o] + p.h_cols[o];
+    }
+    p.lmat_len[l] = tot;
+    p.lidx_len[l] = itot;
+    p.mat_len += tot;
+    p.idx_len += itot;
+    std::vector<double> colmajor;
+    std::vector<int32_t> idx;
+    try { colmajor.resize(2 * (size_t)tot); idx.resize(itot); } catch (...) { s = IDBF_ENOMEM; break; }
+    for (int64_t o = l * nbl; o < (l + 1) * nbl; ++o) {
+      const int64_t r = p.h_rows[o], c = p.h_cols[o];
+      const double* src = f->mat + 2 * f->blk_moff[o];
+      double* dst = colmajor.data() + 2 * p.h_moff[o];
+      for (int64_t i = 0; i < r; ++i)
+        for (int64_t j = 0; j < c; ++j) {
+          dst[2 * (j * r + i)] = src[2 * (i * c + j)];
+          dst[2 * (j * r + i) + 1] = src[2 * (i * c + j) + 1];
+        }
+      if (p.lv[l].kind != KIND_S)
+        memcpy(idx.data() + p.h_ioff[o], f->idx + f->blk_ioff[o], (r + c) * sizeof(int32_t));
+    }
+    cudaError_t e = cudaSuccess;
+    if (tot > 0) {
+      e = cudaMalloc(&p.lmat[IDBF_STORE_C128][l], tot * 16);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(p.lmat[IDBF_STORE_C128][l], colmajor.data(), tot * 16, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess && itot > 0) {
+      e = cudaMalloc(&p.lidx[l], itot * sizeof(int32_t));
+      if (e == cudaSuccess) e = cudaMemcpyAsync(p.lidx[l], idx.data(), itot * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host staging buffers go out of scope
     if (e != cudaSuccess) { set_cuda_error(e); s = e == cudaErrorMemoryAllocation ? IDBF_ENOMEM : IDBF_ECUDA; }
-  } else if (s == IDBF_OK) {
-    p.d_mat[IDBF_STORE_C128] = nullptr;
   }
-  if (s == IDBF_OK && tot > 0 && storage != IDBF_STORE_C128) s = convert_storage(&p, 1u << storage, st);
+  if (s == IDBF_OK) s = upload_structure(&p, st);
+  if (s == IDBF_OK && storage != IDBF_STORE_C128) s = convert_storage(&p, 1u << storage, st);
   if (s == IDBF_OK) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { set_cuda_error(e); s = IDBF_ECUDA; }
@@ -384,7 +421,7 @@ idbf_status idbf_stats(idbf_plan h, idbf_stats_t* s) {
   const Plan& p = h->p;
   memset(s, 0, sizeof(*s));
   s->N = p.N; s->n0 = p.n0; s->L = p.L; s->h_v = p.hV; s->h_u = p.hU;
-  for (int f = 0; f < 3; ++f) if (p.d_mat[f] || (p.mat_len == 0 && f == 0)) s->storage_mask |= 1u << f;
+  for (int f = 0; f < 3; ++f) if (p.has_format(f)) s->storage_mask |= 1u << f;
   s->rank_saturated = p.rank_saturated;
   s->entries = p.mat_len;
   s->index_entries = p.idx_len;
@@ -410,32 +447,44 @@ struct FileHeader {
 idbf_status idbf_save(idbf_plan h, const char* path) {
   if (!h || !path) return IDBF_EINVAL;
   const Plan& p = h->p;
-  const bool have128 = p.d_mat[IDBF_STORE_C128] != nullptr, havedf = p.d_mat[IDBF_STORE_DF64] != nullptr;
+  const bool have128 = p.has_format(IDBF_STORE_C128), havedf = p.has_format(IDBF_STORE_DF64);
   if (p.mat_len > 0 && !have128 && !havedf) return IDBF_EUNSUPPORTED;
-  std::vector<double> dev(2 * (size_t)p.mat_len), rowmajor(2 * (size_t)p.mat_len);
-  if (p.mat_len > 0) {
-    if (have128) {
-      IDBF_CUDA_TRY(cudaMemcpy(dev.data(), p.d_mat[IDBF_STORE_C128], p.mat_len * 16, cudaMemcpyDeviceToHost));
-    } else {
-      std::vector<float> t(4 * (size_t)p.mat_len);
-      IDBF_CUDA_TRY(cudaMemcpy(t.data(), p.d_mat[IDBF_STORE_DF64], p.mat_len * 16, cudaMemcpyDeviceToHost));
-      for (int64_t i = 0; i < p.mat_len; ++i) {
-        dev[2 * i] = (double)t[4 * i] + (double)t[4 * i + 1];
-        dev[2 * i + 1] = (double)t[4 * i + 2] + (double)t[4 * i + 3];
+  const int64_t nbl = (int64_t)p.m * 2, nb = (int64_t)(p.L + 1) * nbl;
+  // file layout: global (not per-level) offsets, row-major blocks
+  std::vector<int64_t> gmoff(nb), gioff(nb);
+  std::vector<double> rowmajor(2 * (size_t)p.mat_len);
+  std::vector<int32_t> idx(p.idx_len);
+  int64_t mbase = 0, ibase = 0;
+  for (int l = 0; l <= p.L; ++l) {
+    const int64_t n = p.lmat_len[l];
+    std::vector<double> dev(2 * (size_t)n);
+    if (n > 0) {
+      if (have128) {
+        IDBF_CUDA_TRY(cudaMemcpy(dev.data(), p.lmat[IDBF_STORE_C128][l], n * 16, cudaMemcpyDeviceToHost));
+      } else {
+        std::vector<float> t(4 * (size_t)n);
+        IDBF_CUDA_TRY(cudaMemcpy(t.data(), p.lmat[IDBF_STORE_DF64][l], n * 16, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n; ++i) {
+          dev[2 * i] = (double)t[4 * i] + (double)t[4 * i + 1];
+          dev[2 * i + 1] = (double)t[4 * i + 2] + (double)t[4 * i + 3];
+        }
       }
     }
+    if (p.lidx_len[l] > 0)
+      IDBF_CUDA_TRY(cudaMemcpy(idx.data() + ibase, p.lidx[l], p.lidx_len[l] * 4, cudaMemcpyDeviceToHost));
+    for (int64_t o = l * nbl; o < (l + 1) * nbl; ++o) {
+      const int64_t r = p.h_rows[o], c = p.h_cols[o], base = p.h_moff[o];
+      gmoff[o] = mbase + base;
+      gioff[o] = ibase + p.h_ioff[o];
+      for (int64_t i = 0; i < r; ++i)
+        for (int64_t j = 0; j < c; ++j) {
+          rowmajor[2 * (mbase + base + i * c + j)] = dev[2 * (base + j * r + i)];
+          rowmajor[2 * (mbase + base + i * c + j) + 1] = dev[2 * (base + j * r + i) + 1];
+        }
+    }
+    mbase += n;
+    ibase += p.lidx_len[l];
   }
-  const int64_t nb = (int64_t)(p.L + 1) * p.m * 2;
-  for (int64_t o = 0; o < nb; ++o) {
-    const int64_t r = p.h_rows[o], c = p.h_cols[o], base = p.h_moff[o];
-    for (int64_t i = 0; i < r; ++i)
-      for (int64_t j = 0; j < c; ++j) {
-        rowmajor[2 * (base + i * c + j)] = dev[2 * (base + j * r + i)];
-        rowmajor[2 * (base + i * c + j) + 1] = dev[2 * (base + j * r + i) + 1];
-      }
-  }
-  std::vector<int32_t> idx(p.idx_len);
-  if (p.idx_len > 0) IDBF_CUDA_TRY(cudaMemcpy(idx.data(), p.d_idx, p.idx_len * 4, cudaMemcpyDeviceToHost));
   FILE* fp = fopen(path, "wb");
   if (!fp) return IDBF_EINVAL;
   FileHeader hd;
@@ -446,8 +495,8 @@ idbf_status idbf_save(idbf_plan h, const char* path) {
   ok = ok && fwrite(p.h_seg_len.data(), 4, ns, fp) == (size_t)ns;
   ok = ok && fwrite(p.h_rows.data(), 4, nb, fp) == (size_t)nb;
   ok = ok && fwrite(p.h_cols.data(), 4, nb, fp) == (size_t)nb;
-  ok = ok && fwrite(p.h_moff.data(), 8, nb, fp) == (size_t)nb;
-  ok = ok && fwrite(p.h_ioff.data(), 8, nb, fp) == (size_t)nb;
+  ok = ok && fwrite(gmoff.data(), 8, nb, fp) == (size_t)nb;
+  ok = ok && fwrite(gioff.data(), 8, nb, fp) == (size_t)nb;
   ok = ok && fwrite(rowmajor.data(), 16, p.mat_len, fp) == (size_t)p.mat_len;
   ok = ok && fwrite(idx.data(), 4, p.idx_len, fp) == (size_t)p.idx_len;
   ok = (fclose(fp) == 0) && ok;
@@ -492,9 +541,10 @@ void idbf_destroy(idbf_plan h) {
   cudaGetDevice(&cur);
   if (cur != p.device) cudaSetDevice(p.device);
   cudaDeviceSynchronize();
-  for (int f = 0; f < 3; ++f) if (p.d_mat[f]) cudaFree(p.d_mat[f]);
+  for (int f = 0; f < 3; ++f)
+    for (void* q : p.lmat[f]) if (q) cudaFree(q);
+  for (int32_t* q : p.lidx) if (q) cudaFree(q);
   if (p.d_meta) cudaFree(p.d_meta);
-  if (p.d_idx) cudaFree(p.d_idx);
   if (p.d_ws) cudaFree(p.d_ws);
   if (cur != p.device) cudaSetDevice(cur);
   delete h;

@@ -1,0 +1,121 @@
+"""The on-device construction (idbf_build) against the oracle's ground truth.
+
+A GPU-built factorization is not bitwise comparable with the oracle's (pivot ties and rounding
+may pick different skeletons), so it is checked by accuracy: the apply must match the dense
+matvec (or the DFT closed form) to the relative error the tolerance allows (10 eps, the bar the
+oracle's own factorizations meet in tests/test_oracle_idbf.py), and structurally against the
+oracle built on the same samples."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1809_10573_gb300 as P
+from oracle import idbf, kernels
+from paper_1809_10573_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def test_dft_matches_fft():
+    N, n0, eps = 1024, 16, 1e-8
+    x, xi = inputs.uniform_grid(N)
+    plan = P.Plan.build(x, xi, eps=eps, leaf=n0, kernel="dft", sign=-1)
+    g = inputs.complex_gaussian(N, 2, seed=3)
+    y = plan.apply(torch.from_numpy(g).cuda()).cpu().numpy()
+    ref = ((-1.0) ** np.arange(N))[:, None] * np.fft.fft(g, axis=0)
+    assert rel(y, ref) < 10 * eps
+    st = plan.stats()
+    assert st["build_seconds"] > 0 and st["entries"] > 0
+
+
+def test_exact_mode_dft():
+    N, n0 = 64, 4
+    x, xi = inputs.uniform_grid(N)
+    plan = P.Plan.build(x, xi, eps=1e-15, leaf=n0, kernel="dft", sign=-1, sampling=P.SAMPLE_ALL)
+    g = inputs.complex_gaussian(N, 1, seed=2)[:, 0]
+    y = plan.apply(torch.from_numpy(g).cuda()).cpu().numpy()
+    assert rel(y, (-1.0) ** np.arange(N) * np.fft.fft(g)) < 1e-12
+
+
+@pytest.mark.parametrize("N,n0,eps,grid,kind,prof,kw", [
+    (4096, 64, 1e-8, "uniform", "fio", 0, dict(oversample=2.0, oversample_leaf=4.0)),   # config 1
+    (2048, 16, 1e-6, "jitter", "dft", 0, {}),                                            # odd L
+    (2048, 8, 1e-6, "uniform", "fio", 1, {}),                                            # Example 1
+])
+def test_accuracy_against_dense(N, n0, eps, grid, kind, prof, kw):
+    x, xi = inputs.uniform_grid(N) if grid == "uniform" else inputs.jittered_grid(N, seed=N)
+    plan = P.Plan.build(x, xi, eps=eps, leaf=n0, kernel=kind, c_profile=prof, sign=-1, **kw)
+    K = kernels.Kernel(kernels.KIND_FIO if kind == "fio" else kernels.KIND_DFT, sign=-1, c_profile=prof)
+    g = inputs.complex_gaussian(N, 1, seed=5)[:, 0]
+    ud = idbf.dense_matvec(K, x, xi, g)
+    gd = torch.from_numpy(g).cuda()
+    assert rel(plan.apply(gd).cpu().numpy(), ud) < 10 * eps
+    # adjoint against the dense K^*
+    Kd = K.entries(x, xi, np.arange(N), np.arange(N))
+    assert rel(plan.apply_adjoint(gd).cpu().numpy(), Kd.conj().T @ g) < 10 * eps
+    # the double-float and FP32 applies of the GPU-built factors
+    plan.set_storage(P.STORE_C128, P.STORE_DF64, P.STORE_C64)
+    y64 = plan.apply(gd).cpu().numpy()
+    assert rel(plan.apply(gd, mode=P.MODE_DF64).cpu().numpy(), y64) < 1e-12
+    assert rel(plan.apply(gd.to(torch.complex64), mode=P.MODE_FP32).cpu().numpy(), y64) < 2e-5
+
+
+def test_random_sampling_follows_the_oracle_streams():
+    # uniform random sampling draws from the same SplitMix64 streams as the oracle, so on the
+    # same candidates both pick the same rows; the ranks then agree up to rare pivot near-ties
+    N, n0, eps = 1024, 16, 1e-7
+    x, xi = inputs.uniform_grid(N)
+    K = kernels.Kernel(kernels.KIND_FIO, c_profile=1)
+    F = idbf.build(K, x, xi, eps, n0, sampler="random", seed=7)
+    plan = P.Plan.build(x, xi, eps=eps, leaf=n0, kernel="fio", c_profile=1, sampling=P.SAMPLE_RANDOM, seed=7)
+    ex = idbf.export(F)
+    st = plan.stats()
+    assert st["L"] == F.L
+    g = inputs.complex_gaussian(N, 1, seed=6)[:, 0]
+    ud = idbf.dense_matvec(K, x, xi, g)
+    e_gpu = rel(plan.apply(torch.from_numpy(g).cuda()).cpu().numpy(), ud)
+    e_cpu = rel(idbf.apply(F, g), ud)
+    assert e_gpu < 10 * max(e_cpu, eps)
+    # stored entries within 2 % of the oracle's
+    assert abs(st["entries"] - ex["mat"].size) <= 0.02 * ex["mat"].size
+
+
+def test_rank_cap_saturation_is_reported():
+    N, n0 = 4096, 64
+    x, xi = inputs.uniform_grid(N)
+    plan = P.Plan.build(x, xi, eps=1e-8, leaf=n0, kernel="fio", c_profile=0, rank_cap=8)
+    assert plan.rank_capped and plan.stats()["rank_saturated"] > 0
+    assert max(plan.stats()["level_kmax"][:-1]) <= 8
+
+
+def test_invalid_inputs():
+    x, xi = inputs.uniform_grid(1024)
+    with pytest.raises(P.IDBFError):
+        P.Plan.build(x[::-1].copy(), xi, leaf=16)          # unsorted points
+    with pytest.raises(P.IDBFError):
+        P.Plan.build(x[:1000], xi[:1000], leaf=16)          # N not n0 2^L
+    with pytest.raises(P.IDBFError):
+        P.Plan.build(x, xi, leaf=512)                       # L = 1
+    with pytest.raises(P.IDBFError):
+        P.Plan.build(x, xi, leaf=16, oversample=0.5)
+
+
+def test_checkpoint_of_a_built_plan(tmp_path):
+    N = 1024
+    x, xi = inputs.uniform_grid(N)
+    plan = P.Plan.build(x, xi, eps=1e-8, leaf=16, kernel="fio", c_profile=1)
+    path = str(tmp_path / "b.idbf")
+    plan.save(path)
+    p2 = P.Plan.load(path, storage=P.STORE_DF64)
+    g = torch.from_numpy(inputs.complex_gaussian(N, 1, seed=9)[:, 0]).cuda()
+    assert rel(p2.apply(g, mode=P.MODE_DF64).cpu().numpy(), plan.apply(g).cpu().numpy()) < 1e-13
