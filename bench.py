@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Throughput of the IDBF apply: applies/s at N = 2^20 on one GB300 (replicas on N GPUs).
+
+Workload (the configuration the headline metric is quoted on): the 1D FIO
+K(x, xi) = exp(2 pi i (x xi + c(x) |xi|)), c(x) = (2 + sin 2 pi x sin 4 pi x) / 3, on the uniform
+grids x_i = i/N, xi_j = j - N/2, N = 2^20, eps = 1e-6, leaf n0 = 64, one complex128 right-hand
+side drawn from a seeded complex Gaussian. The factorization is built on the GPU (untimed);
+a step is one apply y = K x through all L + 1 = 15 butterfly levels.
+
+Modes timed: "df64" (factors as double-float pairs, FP32-pair arithmetic, FP64-class accuracy;
+the headline value), "fp64" (FP64 factors and FMA), "fp32" (complex64 factors and FP32 FMA).
+Each states its relative error against the FP64 apply, and the FP64 apply states eps^a of
+Sec. 3 against dense rows of K x computed directly on the GPU.
+
+`--impl reference` times the CPU oracle instead (see cpu_arm below); there is no other
+implementation to compare with.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")  # the oracle runs single-threaded (the paper's setting)
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_LOG2 = 20     # default; --log2n changes it (smaller cases for profiling)
+LEAF = 64
+EPS = 1e-6
+T_OVERSAMPLE, T_LEAF = 2.0, 4.0
+SEED = 2
+CPU_LOG2 = 14   # the bounded CPU sample: the same workload at N = 2^14
+METRIC = "IDBF applies/s at N=2^20 (FP64 vs split-FP32, rel err stated), % HBM roofline"
+
+
+def workload(log2n):
+    return (f"1D FIO c(x)=(2+sin2pi x sin4pi x)/3, X={{i/N}}, Omega={{j-N/2}}, N=2^{log2n}, eps=1e-6, leaf 64, "
+            "Mock-Chebyshev t=2 (t=4 at the leaf), complex128, 1 RHS (seeded complex Gaussian)")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def read_traffic_summary():
+    """DRAM bytes per algorithmic byte of the level kernel from the committed ncu summary, valid
+    only while the kernel source is the one that was profiled."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "level_kernel_traffic.txt")
+    try:
+        kv = {}
+        for ln in open(path):
+            if "=" in ln and not ln.startswith("#"):
+                k, v = ln.strip().split("=", 1)
+                kv[k.strip()] = v.strip()
+        src = open(os.path.join(ROOT, "paper_1809_10573_gb300", "csrc", "apply.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != kv.get("apply_cu_sha256"):
+            return None
+        return float(kv["dram_bytes_per_algorithmic_byte"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            self.f.flush()
+            self.f.seek(0)
+            for ln in self.f.read().splitlines():
+                p = [x.strip() for x in ln.split(",")]
+                if len(p) >= 10:
+                    rows.append(p)
+            os.unlink(self.f.name)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[4]) for r in rows if r[4].replace(".", "").isdigit()) if rows else None}
+
+
+def dist_init():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend, init_method="env://")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """The slowest rank's time decides the job's time."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, seconds_per_rank: float, world: int) -> tuple:
+    """Whole-job throughput: every rank's units over the slowest rank's time (weak scaling)."""
+    t = max_over_ranks(seconds_per_rank, world)
+    return units_per_rank * world / t, t
+
+
+# ---- CPU oracle (the baseline; the only place bench.py runs oracle/) ------------------------
+def oracle_sample():
+    """The oracle's factorization of the same workload at N = 2^14 (build untimed)."""
+    from oracle import idbf, kernels
+    from paper_1809_10573_gb300 import inputs
+    N = 1 << CPU_LOG2
+    x, xi = inputs.uniform_grid(N)
+    F = idbf.build(kernels.Kernel(kernels.KIND_FIO, c_profile=0), x, xi, EPS, LEAF, t=T_OVERSAMPLE, t_leaf=T_LEAF)
+    g = inputs.complex_gaussian(N, 1, seed=SEED)[:, 0]
+    return F, g
+
+
+def nlogn_scale():
+    """Work of one N = 2^log2n apply over one N = 2^14 apply, O(N log N) (Sec. 1)."""
+    return ((1 << N_LOG2) * N_LOG2) / ((1 << CPU_LOG2) * CPU_LOG2)
+
+
+def cpu_time_applies(F, g, reps=None, budget_s=10.0):
+    from oracle import idbf
+    idbf.apply(F, g)
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while (reps is None and time.perf_counter() < t_end) or (reps is not None and len(times) < reps):
+        t0 = time.perf_counter()
+        idbf.apply(F, g)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def cpu_baseline():
+    F, g = oracle_sample()
+    times = cpu_time_applies(F, g)
+    t = statistics.median(times)
+    return {"value": 1.0 / (t * nlogn_scale()), "unit": "applies/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle FP64 apply (numpy, 1 thread) of the same workload at N=2^{CPU_LOG2} "
+                       f"(factors built by the oracle, untimed), median of {len(times)} applies = {t*1e3:.1f} ms, "
+                       f"scaled to one N=2^{N_LOG2} apply by the N log N work ratio {nlogn_scale():.1f}")}
+
+
+def cpu_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    F, g = oracle_sample()
+    cpu_time_applies(F, g, reps=args.warmup)
+    t0 = time.perf_counter()
+    cpu_time_applies(F, g, reps=args.steps)
+    dt = time.perf_counter() - t0
+    per = dt / args.steps
+    value = 1.0 / (per * nlogn_scale())
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3 * nlogn_scale(),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload(N_LOG2)},
+            "cpu_baseline": {"value": value, "unit": "applies/s", "cores": 1, "kind": "oracle",
+                             "sample": (f"each step: one oracle FP64 apply at N=2^{CPU_LOG2} of the same workload "
+                                        f"({per*1e3:.1f} ms), scaled by the N log N work ratio {nlogn_scale():.1f}")},
+            "e2e": {"value": value, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- GPU arm ---------------------------------------------------------------------------------
+def gpu_arm(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1809_10573_gb300 as P
+    from paper_1809_10573_gb300 import inputs
+
+    N = 1 << N_LOG2
+    x, xi = inputs.uniform_grid(N)
+    t0 = time.time()
+    plan = P.Plan.build(x, xi, eps=EPS, leaf=LEAF, kernel="fio", c_profile=0, oversample=T_OVERSAMPLE,
+                        oversample_leaf=T_LEAF)
+    build_s = time.time() - t0
+    want = set(args.modes.split(","))
+    fmts = [f for name, f in (("fp64", P.STORE_C128), ("df64", P.STORE_DF64), ("fp32", P.STORE_C64)) if name in want]
+    if "df64" not in want:
+        raise SystemExit("the headline mode df64 must be among --modes")
+    if "fp64" not in want:   # the FP64 reference result is computed before the C128 copy goes
+        fmts_final = fmts
+        fmts = sorted(set(fmts) | {P.STORE_C128})
+    else:
+        fmts_final = fmts
+    plan.set_storage(*fmts)
+    st = plan.stats()
+    L = st["L"]
+    g = inputs.complex_gaussian(N, 1, seed=SEED)[:, 0]
+    gd = torch.from_numpy(g).cuda()
+    g32 = gd.to(torch.complex64)
+    stream = torch.cuda.current_stream()
+
+    # accuracy: eps^a of the FP64 apply on 256 sampled rows against the direct matvec (Sec. 3),
+    # and each mode against the FP64 apply
+    y64 = plan.apply(gd, mode=P.MODE_FP64)
+    rows = inputs.sample_rows(N, 256, seed=SEED)
+    ud = P.kernel_matvec_rows(torch.from_numpy(x).cuda(), torch.from_numpy(xi).cuda(), gd,
+                              torch.from_numpy(rows).cuda(), kernel="fio", c_profile=0)
+    eps_a = float(torch.linalg.norm(y64[torch.from_numpy(rows).cuda()] - ud) / torch.linalg.norm(ud))
+    ydf = plan.apply(gd, mode=P.MODE_DF64)
+    y32 = plan.apply(g32, mode=P.MODE_FP32) if "fp32" in want else None
+    nrm = torch.linalg.norm(y64)
+    rel_df = float(torch.linalg.norm(ydf - y64) / nrm)
+    rel_32 = float(torch.linalg.norm(y32.to(torch.complex128) - y64) / nrm) if "fp32" in want else None
+    plan.set_storage(*fmts_final)
+
+    def timed(mode, vec, steps, warmup, sampler_index=None):
+        for _ in range(warmup):
+            plan.apply(vec, mode=mode, out=ybuf[mode])
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.apply(vec, mode=mode, out=ybuf[mode])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return e0.elapsed_time(e1) / 1e3
+
+    ybuf = {P.MODE_FP64: torch.empty_like(gd), P.MODE_DF64: torch.empty_like(gd), P.MODE_FP32: torch.empty_like(g32)}
+    modes = {}
+    for name, mode, vec, eb in (("fp64", P.MODE_FP64, gd, 16), ("fp32", P.MODE_FP32, g32, 8)):
+        if name not in want:
+            continue
+        secs = timed(mode, vec, max(5, args.steps // 2), args.warmup)
+        n = max(5, args.steps // 2)
+        ab = plan.algorithmic_bytes(1, eb, eb)
+        modes[name] = {"applies_per_s": n / secs, "ms_per_apply": secs / n * 1e3,
+                       "algorithmic_GBps": ab * n / secs / 1e9,
+                       "rel_err_vs_fp64": 0.0 if name == "fp64" else rel_32}
+    # headline: double-float, clocks sampled during the timed region
+    with ClockSampler(torch.cuda.current_device()) as cs:
+        secs = timed(P.MODE_DF64, gd, args.steps, args.warmup)
+    clocks = cs.summary()
+    value, tmax = job_throughput(args.steps, secs, world)
+    ms = tmax / args.steps * 1e3
+    ab = plan.algorithmic_bytes(1, 16, 16)
+    modes["df64"] = {"applies_per_s": args.steps / secs, "ms_per_apply": secs / args.steps * 1e3,
+                     "algorithmic_GBps": ab * args.steps / secs / 1e9, "rel_err_vs_fp64": rel_df}
+    peak, peak_kind = peaks()
+    achieved = ab / (secs / args.steps) / 1e9   # all L+1 launches are the level kernel
+    ratio = read_traffic_summary()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": peak_kind,
+                "traffic": (ratio * ab / (L + 1)) if ratio is not None else None,
+                "kernel": "k_level_fwd<DF64P,1> (every launch of the timed region)",
+                "algorithmic_bytes_per_launch": ab / (L + 1)}
+    # end to end through the C call: pinned host x -> device, apply, device -> host y
+    xh = torch.from_numpy(g.copy()).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xdev = torch.empty_like(gd)
+    ydev = torch.empty_like(gd)
+
+    def e2e_step():
+        xdev.copy_(xh, non_blocking=True)
+        plan.apply(xdev, mode=P.MODE_DF64, out=ydev)
+        yh.copy_(ydev, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_secs = e0.elapsed_time(e1) / 1e3
+    e2e_value, _ = job_throughput(args.steps, e2e_secs, world)
+    if not torch.allclose(yh.cuda(), ydf):
+        raise RuntimeError("end-to-end result differs from the device apply")
+    cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu) else None
+    line = {"metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32x2", "data": "synthetic",
+            "config": {"workload": workload(N_LOG2), "N": N, "eps": EPS, "leaf": LEAF, "nrhs": 1,
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": f"inputs larger than L2: {st['entries']*16/1e9:.1f} GB of factors per apply"},
+            "rel_err": {"eps_a_fp64_vs_dense_256_rows": eps_a, "df64_vs_fp64": rel_df, "fp32_vs_fp64": rel_32},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "applies/s", "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
+            "gpu_launches": (L + 1) * args.steps, "clocks": clocks, "modes": modes,
+            "build": {"seconds": build_s, "entries": st["entries"], "levels": L + 1,
+                      "level_kmax": st["level_kmax"], "rank_saturated": st["rank_saturated"],
+                      "device_GB": st["device_bytes"] / 1e9}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--log2n", type=int, default=20, help="N = 2^log2n (20 = the benchmarked workload)")
+    ap.add_argument("--modes", default="df64,fp64,fp32", help="apply modes to time (df64 is the headline)")
+    args = ap.parse_args()
+    global N_LOG2
+    N_LOG2 = args.log2n
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    rank, world, local = dist_init()
+    try:
+        if args.impl == "reference":
+            return cpu_arm(args, rank, world)
+        return gpu_arm(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -112,6 +112,15 @@ void idbf_default_params(idbf_params* p);
 idbf_status idbf_build(const idbf_kernel* kernel, const double* x_host, const double* xi_host,
                        int64_t N, const idbf_params* params, void* stream, idbf_plan* out);
 
+/* idbf_kernel_matvec_rows - ground truth of Sec. 3 (the direct matvec u^d) on selected rows:
+ *   y[r] = sum_{j < N} K(x[rows[r]], xi[j]) v[j],  r < nrows,
+ * O(nrows N) FP64 work on the current device. x, xi: N doubles; rows: nrows int64 row indices
+ * (< N, not checked on the device); v: N complex128; y: nrows complex128; all device pointers.
+ * Stream-ordered. Errors: EINVAL, ECUDA. */
+idbf_status idbf_kernel_matvec_rows(const idbf_kernel* kernel, const double* x, const double* xi,
+                                    int64_t N, const int64_t* rows, int64_t nrows, const void* v,
+                                    void* y, void* stream);
+
 /* ---- import of host factors in the butterfly layout (used for oracle parity) ----------- */
 typedef struct {
   int64_t N;

@@ -17,7 +17,7 @@ from ._lib import (KERNEL_DFT, KERNEL_FIO1D, MODE_DF64, MODE_FP32, MODE_FP64, MO
                    SAMPLE_ALL, SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, STORE_C64, STORE_C128,
                    STORE_DF64, IDBFError)
 
-__all__ = ["Plan", "IDBFError", "apply", "IDBFApply", "KERNEL_FIO1D", "KERNEL_DFT", "MODE_FP64",
+__all__ = ["Plan", "IDBFError", "apply", "IDBFApply", "kernel_matvec_rows", "KERNEL_FIO1D", "KERNEL_DFT", "MODE_FP64",
            "MODE_DF64", "MODE_FP32", "MODE_TF32X3", "STORE_C128", "STORE_DF64", "STORE_C64",
            "SAMPLE_MOCK_CHEBYSHEV", "SAMPLE_RANDOM", "SAMPLE_ALL"]
 
@@ -169,6 +169,20 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def kernel_matvec_rows(x, xi, v, rows, kernel="fio", c_profile=0, sign=-1, stream=None):
+    """Direct (dense) rows of K v on the GPU: the ground truth u^d of Sec. 3 at `rows`.
+    x, xi: float64 CUDA tensors; v: complex128 CUDA tensor (N,); rows: int64 CUDA tensor."""
+    k = _lib.Kernel(KERNEL_FIO1D if kernel == "fio" else KERNEL_DFT, sign, c_profile, 0)
+    y = torch.empty(rows.numel(), dtype=torch.complex128, device=v.device)
+    for t, dt in ((x, torch.float64), (xi, torch.float64), (v, torch.complex128), (rows, torch.int64)):
+        if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError("kernel_matvec_rows: expected contiguous CUDA tensors of the documented dtypes")
+    _lib.check(_lib.lib().idbf_kernel_matvec_rows(C.byref(k), x.data_ptr(), xi.data_ptr(), x.numel(), rows.data_ptr(),
+                                                   rows.numel(), v.data_ptr(), y.data_ptr(), _stream_ptr(stream)),
+               "idbf_kernel_matvec_rows")
+    return y
 
 
 def apply(plan: Plan, x, mode=MODE_FP64):

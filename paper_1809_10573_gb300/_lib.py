@@ -52,6 +52,8 @@ SIGNATURES = {
     "idbf_default_params": (None, [C.POINTER(Params)]),
     "idbf_build": (C.c_int, [C.POINTER(Kernel), C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(Params),
                              C.c_void_p, C.POINTER(C.c_void_p)]),
+    "idbf_kernel_matvec_rows": (C.c_int, [C.POINTER(Kernel), C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                          C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "idbf_import_factors": (C.c_int, [C.POINTER(HostFactors), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
     "idbf_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),
     "idbf_apply_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,

@@ -892,10 +892,54 @@ idbf_status Builder::assemble() {
   return upload_structure(&P, st);
 }
 
+// dense ground-truth rows: y[r] = sum_j K(x[rows[r]], xi[j]) v[j], FP64, a block per row
+__global__ void k_dense_rows(KDesc K, const double* __restrict__ x, const double* __restrict__ xi, int64_t N,
+                             const int64_t* __restrict__ rows, const double2* __restrict__ v, double2* __restrict__ y) {
+  __shared__ double2 red[32];
+  const int64_t r = rows[blockIdx.x];
+  const double xr = x[r];
+  double c = 0.0;
+  if (K.kind == IDBF_KERNEL_FIO1D) {
+    if (K.prof == 0) c = (2.0 + sinpi(2.0 * xr) * sinpi(4.0 * xr)) / 3.0;
+    else if (K.prof == 1) c = (2.0 + 0.2 * sinpi(2.0 * xr)) / 16.0;
+  }
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    const double2 k = kentry(K, xr, c, xi[j]);
+    const double2 b = v[j];
+    acc.x = fma(k.x, b.x, fma(-k.y, b.y, acc.x));
+    acc.y = fma(k.x, b.y, fma(k.y, b.x, acc.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t.x += red[w].x; t.y += red[w].y; }
+    y[blockIdx.x] = t;
+  }
+}
+
 }  // namespace bld
 }  // namespace idbf
 
 using namespace idbf;
+
+extern "C" idbf_status idbf_kernel_matvec_rows(const idbf_kernel* kernel, const double* x, const double* xi, int64_t N,
+                                               const int64_t* rows, int64_t nrows, const void* v, void* y,
+                                               void* stream) {
+  if (!kernel || !x || !xi || !rows || !v || !y || N < 1 || nrows < 0 || nrows > (1LL << 31) - 1) return IDBF_EINVAL;
+  if (kernel->kind != IDBF_KERNEL_FIO1D && kernel->kind != IDBF_KERNEL_DFT) return IDBF_EINVAL;
+  if (nrows == 0) return IDBF_OK;
+  bld::KDesc K{kernel->kind, kernel->sign, kernel->c_profile};
+  bld::k_dense_rows<<<(unsigned)nrows, 256, 0, (cudaStream_t)stream>>>(K, x, xi, N, rows, (const double2*)v, (double2*)y);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_cuda_error(e); return IDBF_ECUDA; }
+  return IDBF_OK;
+}
 
 extern "C" idbf_status idbf_build(const idbf_kernel* kernel, const double* x_host, const double* xi_host, int64_t N,
                                   const idbf_params* params, void* stream, idbf_plan* out) {

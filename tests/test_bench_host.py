@@ -1,0 +1,64 @@
+"""Host-side logic of bench.py: whole-job throughput over ranks (gloo, world size 2 on CPU),
+the clock-record parsing, and the traffic summary's validity check."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    secs = [2.0, 3.0][rank]                  # the slower rank decides
+    value, t = bench.job_throughput(10, secs, world)
+    bench.barrier(world)
+    q.put((rank, value, t))
+    dist.destroy_process_group()
+
+
+def test_job_throughput_takes_the_slowest_rank():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    for _, value, t in out:
+        assert t == 3.0 and abs(value - 20 / 3.0) < 1e-12
+
+
+def test_single_rank_throughput():
+    assert bench.job_throughput(5, 2.0, 1) == (2.5, 2.0)
+
+
+def test_clock_summary_parsing(tmp_path):
+    cs = bench.ClockSampler(0)
+    f = tmp_path / "c.csv"
+    f.write_text("2026/12/03 01:00:00.000, 0, 1900, 2070, 900.5, 0x4, Not Active, Not Active, Not Active, Active\n"
+                 "2026/12/03 01:00:00.200, 0, 1950, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    cs.f = open(f, "r+")
+    s = cs.summary()
+    assert s["samples"] == 2 and s["sm_mhz"] == 1925 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_traffic_summary_requires_the_profiled_source(tmp_path, monkeypatch):
+    v = bench.read_traffic_summary()
+    assert v is None or v > 0
