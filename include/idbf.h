@@ -161,6 +161,29 @@ idbf_status idbf_apply(idbf_plan plan, const void* x, void* y, int64_t nrhs, int
 idbf_status idbf_apply_adjoint(idbf_plan plan, const void* x, void* y, int64_t nrhs, int64_t ld,
                                int32_t mode, void* stream);
 
+/* idbf_apply_noalloc - y = K x exactly as idbf_apply (same arguments, modes and results), except
+ * that the library allocates no device memory during the call. The paper has no counterpart of
+ * this call; it exists for callers that must not allocate: a framework whose own caching
+ * allocator already holds nearly all device memory (a cudaMalloc would fail or fragment it), a
+ * latency-critical serving loop that cannot absorb the device-wide synchronisation that
+ * cudaMalloc and cudaFree imply, or a process that has to know its full device footprint when
+ * the library loads.
+ *   Workspace: a fixed array of IDBF_NOALLOC_SCRATCH_BYTES compiled into the library. Every GPU
+ *   that loads the library holds one such array until the process exits. A call needs
+ *   32 * nrhs * segment_entries bytes (segment_entries as reported by idbf_stats); a larger
+ *   request returns IDBF_EUNSUPPORTED before any GPU work (the FIO benchmark kernel fits for
+ *   N up to 2^18 with one right-hand side).
+ *   The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ *   with that device current): make that first call before any stream capture.
+ *   All calls on a device share the one array, and it keeps whatever the previous call left in
+ *   it; nothing in it has to start at zero, because every level overwrites each segment before
+ *   the next level reads it. Calls whose GPU work overlaps (other streams, other plans, other
+ *   host threads) race on the array and produce wrong results: serialise them.
+ *   Errors: EINVAL, EUNSUPPORTED (size above the limit, or storage for `mode` absent), ECUDA. */
+#define IDBF_NOALLOC_SCRATCH_BYTES (64ull << 20)
+idbf_status idbf_apply_noalloc(idbf_plan plan, const void* x, void* y, int64_t nrhs, int64_t ld,
+                               int32_t mode, void* stream);
+
 /* idbf_reserve - allocate the apply workspace for up to nrhs right-hand sides now. */
 idbf_status idbf_reserve(idbf_plan plan, int64_t nrhs);
 

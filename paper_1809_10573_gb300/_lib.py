@@ -17,6 +17,7 @@ SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, SAMPLE_ALL = 0, 1, 2
 STORE_C128, STORE_DF64, STORE_C64 = 0, 1, 2
 MODE_FP64, MODE_DF64, MODE_FP32, MODE_TF32X3 = 0, 1, 2, 3
 MAX_LEVELS = 48
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 class Kernel(C.Structure):
@@ -57,6 +58,8 @@ SIGNATURES = {
     "idbf_import_factors": (C.c_int, [C.POINTER(HostFactors), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
     "idbf_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),
     "idbf_apply_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
+                                     C.c_void_p]),
+    "idbf_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
                                      C.c_void_p]),
     "idbf_reserve": (C.c_int, [C.c_void_p, C.c_int64]),
     "idbf_set_storage": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p]),

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "idbf_internal.h"
 
@@ -565,6 +566,63 @@ static idbf_status apply_common(idbf_plan h, const void* x, void* y, int64_t nrh
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Allocation-free forward apply (idbf_apply_noalloc). The level-to-level workspace is a fixed
+// array compiled into the library instead of the plan's cudaMalloc'ed workspace. In host code
+// the symbol below is only a host-side stand-in: its device address is looked up once per
+// device with cudaGetSymbolAddress and cached.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[IDBF_NOALLOC_SCRATCH_BYTES];
+
+static constexpr int kNoallocMaxDevices = 64;
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up on first use).
+static idbf_status noalloc_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kNoallocMaxDevices) return IDBF_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      set_cuda_error(e);
+      return IDBF_ECUDA;
+    }
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = g_noalloc_addr[dev];
+  return IDBF_OK;
+}
+
+// The forward level loop of run_levels with the two ping-pong buffers placed in `ws`.
+template <class P, int RB>
+static idbf_status run_levels_scratch(Plan* p, const void* x, void* y, int64_t R, int64_t ld, cudaStream_t st,
+                                      int fmt, void* ws) {
+  using V = typename P::vec_t;
+  V* wb[2] = {(V*)ws, (V*)((char*)ws + (size_t)p->max_seg_total * R * 16)};
+  for (int l = 0; l <= p->L; ++l) {
+    const LevelInfo& li = p->lv[l];
+    const DevLevel d = p->level(l);
+    const typename P::mat_t* mat = (const typename P::mat_t*)p->lmat[fmt][l];
+    IO<V> io;
+    io.x = (const V*)x; io.ldx = ld; io.y = (V*)y; io.ldy = ld; io.R = (int)R;
+    io.win = l > 0 ? wb[(l - 1) & 1] : nullptr;
+    io.wout = l < p->L ? wb[l & 1] : nullptr;
+    const int gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
+    const int rcap = std::max(li.max_rows, li.max_cols);
+    dim3 grid((unsigned)p->m, (unsigned)((R + RB - 1) / RB));
+    const size_t sm = (size_t)RB * (li.max_in * sizeof(V) + 2 * gcap * sizeof(typename P::gv_t) +
+                                    2 * rcap * sizeof(V) + li.max_out * sizeof(V));
+    if (sm > 200 * 1024) return IDBF_EUNSUPPORTED;
+    if (sm > 48 * 1024) IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_fwd<P, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int threads = ((li.max_rows_pair + 31) / 32) * 32;
+    threads = std::max(64, std::min(512, threads));
+    k_level_fwd<P, RB><<<grid, threads, sm, st>>>(d, mat, io, gcap, rcap, li.max_in);
+    IDBF_CUDA_TRY(cudaGetLastError());
+  }
+  return IDBF_OK;
+}
+
 }  // namespace idbf
 
 extern "C" {
@@ -576,6 +634,40 @@ idbf_status idbf_apply(idbf_plan h, const void* x, void* y, int64_t nrhs, int64_
 idbf_status idbf_apply_adjoint(idbf_plan h, const void* x, void* y, int64_t nrhs, int64_t ld, int32_t mode,
                                void* stream) {
   return idbf::apply_common(h, x, y, nrhs, ld, mode, stream, true);
+}
+
+idbf_status idbf_apply_noalloc(idbf_plan h, const void* x, void* y, int64_t nrhs, int64_t ld, int32_t mode,
+                               void* stream) {
+  using namespace idbf;
+  if (!h || !x || !y || nrhs < 1 || nrhs > (1 << 20)) return IDBF_EINVAL;
+  Plan* p = &h->p;
+  if (ld < p->N) return IDBF_EINVAL;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != p->device) return IDBF_EINVAL;
+  int fmt;
+  switch (mode) {
+    case IDBF_MODE_FP64: fmt = IDBF_STORE_C128; break;
+    case IDBF_MODE_DF64: fmt = IDBF_STORE_DF64; break;
+    case IDBF_MODE_FP32: fmt = IDBF_STORE_C64; break;
+    default: return IDBF_EINVAL;
+  }
+  if (!p->has_format(fmt)) return IDBF_EUNSUPPORTED;
+  // two ping-pong buffers of the largest boundary, 16 bytes per element and right-hand side
+  const unsigned long long need = 2ull * (unsigned long long)p->max_seg_total * (unsigned long long)nrhs * 16ull;
+  if (need > IDBF_NOALLOC_SCRATCH_BYTES) return IDBF_EUNSUPPORTED;
+  void* ws = nullptr;
+  const idbf_status s = noalloc_scratch(cur, &ws);
+  if (s != IDBF_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool one = nrhs == 1;
+  switch (mode) {
+    case IDBF_MODE_FP64: return one ? run_levels_scratch<FP64P, 1>(p, x, y, nrhs, ld, st, fmt, ws)
+                                    : run_levels_scratch<FP64P, 4>(p, x, y, nrhs, ld, st, fmt, ws);
+    case IDBF_MODE_DF64: return one ? run_levels_scratch<DF64P, 1>(p, x, y, nrhs, ld, st, fmt, ws)
+                                    : run_levels_scratch<DF64P, 4>(p, x, y, nrhs, ld, st, fmt, ws);
+    default: return one ? run_levels_scratch<FP32P, 1>(p, x, y, nrhs, ld, st, fmt, ws)
+                        : run_levels_scratch<FP32P, 4>(p, x, y, nrhs, ld, st, fmt, ws);
+  }
 }
 
 }  // extern "C"
