@@ -192,6 +192,17 @@ idbf_status idbf_reserve(idbf_plan plan, int64_t nrhs);
  * only one of them is kept). Stream-ordered; ENOMEM leaves the plan unchanged. */
 idbf_status idbf_set_storage(idbf_plan plan, uint32_t mask, void* stream);
 
+/* idbf_sync_status - wait for `stream`, then report whether any bounded device-side wait of this
+ * plan's kernels gave up since the last call (IDBF_ETIMEOUT; the outputs of those calls are
+ * invalid) and clear the record. Every wait in the library's kernels ends after a time limit
+ * instead of hanging; IDBF_OK otherwise. */
+idbf_status idbf_sync_status(idbf_plan plan, void* stream);
+
+/* idbf_debug_set_wait - fault injection for tests: set the time limit of the device-side waits
+ * (default 2 s) and, with producer_enabled = 0, make the streaming kernels' producer issue no
+ * copies so that every consumer wait runs out. Not for production use. */
+idbf_status idbf_debug_set_wait(idbf_plan plan, uint64_t limit_ns, int32_t producer_enabled);
+
 /* ---- statistics ------------------------------------------------------------------------- */
 #define IDBF_MAX_LEVELS 48
 typedef struct {

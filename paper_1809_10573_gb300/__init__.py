@@ -134,6 +134,10 @@ class Plan:
         return _lib.check(fn(self._h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), nrhs, ld, mode, C.c_void_p(stream_ptr)),
                           fn.__name__)
 
+    def sync_status(self, stream=None):
+        """Wait for the stream; raise IDBFError(ETIMEOUT) if a device-side wait gave up."""
+        _lib.check(_lib.lib().idbf_sync_status(self._h, _stream_ptr(stream)), "idbf_sync_status")
+
     def reserve(self, nrhs: int):
         _lib.check(_lib.lib().idbf_reserve(self._h, nrhs), "idbf_reserve")
 

@@ -62,6 +62,8 @@ SIGNATURES = {
     "idbf_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
                                      C.c_void_p]),
     "idbf_reserve": (C.c_int, [C.c_void_p, C.c_int64]),
+    "idbf_sync_status": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "idbf_debug_set_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32]),
     "idbf_set_storage": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p]),
     "idbf_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "idbf_save": (C.c_int, [C.c_void_p, C.c_char_p]),

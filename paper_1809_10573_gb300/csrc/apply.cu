@@ -475,6 +475,277 @@ __global__ void __launch_bounds__(256) k_level_adj(DevLevel d, const typename P:
 }
 
 // ---------------------------------------------------------------------------------------------
+// Streaming forward level kernel (one right-hand side). Persistent CTAs (two per SM), each a
+// producer warp and NCW consumer warps. The producer copies every block of its nodes, a few
+// whole columns at a time, with cp.async.bulk into a ring of STAGES shared-memory stages
+// (mbarrier full / empty pairs); the consumers, one output row per thread, multiply the staged
+// columns with the gathered input held in shared memory. Each block is read from HBM once, in
+// large contiguous pieces, while the arithmetic runs from shared memory.
+// Every wait is bounded (globaltimer): on a timeout the CTA sets bit 0 of *status, lets its
+// copies in flight land, and leaves; the host reads the status with idbf_sync_status.
+namespace strm {
+constexpr int NCW = 6;
+constexpr int NCT = NCW * 32;
+constexpr int NTHREADS = NCT + 32;
+constexpr int STAGES = 3;
+constexpr int STAGE_BYTES = 24 * 1024;
+constexpr int RPT = 2;  // output rows per consumer thread: rows <= RPT * NCT
+
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t tx) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(tx) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(sa(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sa(dst)),
+               "l"(src), "r"(bytes), "r"(sa(bar))
+               : "memory");
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NCT) : "memory"); }
+
+// Wait until phase `parity` of barrier b has completed, giving up after limit_ns or when
+// another warp has flagged an abort.
+__device__ __forceinline__ bool wait_bounded(uint64_t* b, uint32_t parity, uint64_t limit_ns, volatile int* abort_flag) {
+  if (mbar_try_wait(b, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_wait(b, parity)) {
+    if (*abort_flag || gtimer() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+// columns per chunk for a block with `rows` rows and elements of es bytes; 8-byte elements may
+// start 8 bytes past a 16-byte boundary, which costs up to two elements of slack
+__host__ __device__ __forceinline__ int cols_per_chunk(int rows, int es) {
+  const int cap = STAGE_BYTES / es - (es == 8 ? 2 : 0);
+  return max(1, cap / max(rows, 1));
+}
+
+struct Geo {
+  size_t vec_off, g_off, res_off, t_off, bar_off, total;
+};
+template <class P>
+__host__ __device__ inline Geo geometry(int max_in, int max_out, int gcap, int rcap) {
+  using V = typename P::vec_t;
+  using G = typename P::gv_t;
+  Geo q;
+  q.vec_off = (size_t)STAGES * STAGE_BYTES;
+  q.g_off = q.vec_off + (((size_t)max_in * sizeof(V) + 127) & ~(size_t)127);
+  q.res_off = q.g_off + (((size_t)2 * gcap * sizeof(G) + 127) & ~(size_t)127);
+  q.t_off = q.res_off + (((size_t)2 * rcap * sizeof(V) + 127) & ~(size_t)127);
+  q.bar_off = q.t_off + (((size_t)max_out * sizeof(V) + 127) & ~(size_t)127);
+  q.total = q.bar_off + 2 * STAGES * sizeof(uint64_t);
+  return q;
+}
+}  // namespace strm
+
+template <class P>
+__global__ void __launch_bounds__(strm::NTHREADS, 2)
+    k_level_stream(DevLevel d, const typename P::mat_t* __restrict__ mat, IO<typename P::vec_t> io, int gcap, int rcap,
+                   int max_in, int max_out, int* __restrict__ status, uint64_t limit_ns, int producer_enabled) {
+  using namespace strm;
+  using V = typename P::vec_t;
+  using G = typename P::gv_t;
+  using M = typename P::mat_t;
+  constexpr int ES = (int)sizeof(M);
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Geo geo = geometry<P>(max_in, max_out, gcap, rcap);
+  unsigned char* stages = smem;
+  V* u = (V*)(smem + geo.vec_off);
+  G* g = (G*)(smem + geo.g_off);
+  V* res = (V*)(smem + geo.res_off);
+  V* t = (V*)(smem + geo.t_off);
+  uint64_t* full = (uint64_t*)(smem + geo.bar_off);
+  uint64_t* empty = full + STAGES;
+  // abort_flag: any warp, only shortens waits. cons_abort: written by consumers before a
+  // consumer barrier and read after it, so that all consumer warps leave the loop together.
+  __shared__ int abort_flag;
+  __shared__ int cons_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], NCW);
+    }
+    abort_flag = 0;
+    cons_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane != 0) return;
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t j = blockIdx.x; j < d.m && ok; j += gridDim.x) {
+      for (int c = 0; c < 2 && ok; ++c) {
+        const int rows = d.rows[2 * j + c], cols = d.cols[2 * j + c];
+        if (rows == 0 || cols == 0) continue;
+        const int cpc = cols_per_chunk(rows, ES);
+        const unsigned char* base = (const unsigned char*)(mat + d.moff[2 * j + c]);
+        for (int j0 = 0; j0 < cols; j0 += cpc, ++it) {
+          const int nc = min(cpc, cols - j0);
+          const int stg = it % STAGES;
+          const uint32_t use = it / STAGES;
+          if (!wait_bounded(&empty[stg], (use & 1) ^ 1, limit_ns, &abort_flag)) { ok = false; break; }
+          const unsigned char* src = base + (size_t)j0 * rows * ES;
+          const unsigned char* src_al = (const unsigned char*)((uintptr_t)src & ~(uintptr_t)15);
+          const unsigned char* end = src + (size_t)nc * rows * ES;
+          const uint32_t bytes = (uint32_t)((((uintptr_t)end + 15) & ~(uintptr_t)15) - (uintptr_t)src_al);
+          if (producer_enabled) {
+            mbar_expect_tx(&full[stg], bytes);
+            bulk_g2s(stages + (size_t)stg * STAGE_BYTES, src_al, bytes, &full[stg]);
+          }
+        }
+      }
+    }
+    if (!ok) {
+      atomicOr(status, 1);
+      abort_flag = 1;
+      // let the copies already issued land before the CTA's shared memory goes away
+      for (uint32_t k = it > STAGES ? it - STAGES : 0; k < it; ++k) {
+        const uint64_t t0 = gtimer();
+        while (!mbar_try_wait(&full[k % STAGES], (k / STAGES) & 1) && gtimer() - t0 < limit_ns) {
+        }
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  const int tc = threadIdx.x - 32;
+  const int cw = warp - 1;
+  (void)cw;
+  uint32_t it = 0;
+  for (int64_t j = blockIdx.x; j < d.m; j += gridDim.x) {
+    consumer_sync();
+    if (*(volatile int*)&cons_abort) break;
+    int l0, l1;
+    if (d.lev == 0) {
+      l0 = d.n0;
+      l1 = 0;
+      for (int i = tc; i < l0; i += NCT) u[i] = io.x[j * d.n0 + i];
+    } else {
+      l0 = d.in_len[2 * j];
+      l1 = d.in_len[2 * j + 1];
+      const int64_t o0 = d.in_off[2 * j];  // segments 2j and 2j+1 are adjacent
+      for (int i = tc; i < l0 + l1; i += NCT) u[i] = io.win[o0 + i];
+    }
+    const int rows0 = d.rows[2 * j], rows1 = d.rows[2 * j + 1];
+    const int cols0 = d.cols[2 * j], cols1 = d.cols[2 * j + 1];
+    const int32_t* ix0 = d.idx + d.ioff[2 * j];
+    const int32_t* ix1 = d.idx + d.ioff[2 * j + 1];
+    consumer_sync();
+    if (d.kind == KIND_V) {
+      for (int i = tc; i < cols0; i += NCT) g[i] = P::cvt(u[ix0[rows0 + i]]);
+      for (int i = tc; i < cols1; i += NCT) g[gcap + i] = P::cvt(u[ix1[rows1 + i]]);
+    } else if (d.kind == KIND_S) {
+      for (int i = tc; i < l0 + l1; i += NCT) g[i] = P::cvt(u[i]);
+    } else {
+      for (int i = tc; i < l0 + l1; i += NCT) g[i < l0 ? i : gcap + i - l0] = P::cvt(u[i]);
+    }
+    consumer_sync();
+    bool failed = false;
+    for (int c = 0; c < 2; ++c) {
+      const int rows = c ? rows1 : rows0, cols = c ? cols1 : cols0;
+      const G* gc = g + (d.kind == KIND_S ? 0 : c * gcap);
+      typename P::acc_t acc[RPT];
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) P::init(acc[k]);
+      if (rows > 0 && cols > 0) {
+        const int cpc = cols_per_chunk(rows, ES);
+        const uintptr_t base = (uintptr_t)(mat + d.moff[2 * j + c]);
+        for (int j0 = 0; j0 < cols; j0 += cpc, ++it) {
+          const int nc = min(cpc, cols - j0);
+          const int stg = it % STAGES;
+          if (!failed && !wait_bounded(&full[stg], (it / STAGES) & 1, limit_ns, &abort_flag)) failed = true;
+          if (!failed) {
+            const uintptr_t src = base + (uintptr_t)j0 * rows * ES;
+            const int shift = (int)((src & 15) / ES);
+            const M* st = (const M*)(stages + (size_t)stg * STAGE_BYTES) + shift;
+#pragma unroll 4
+            for (int jj = 0; jj < nc; ++jj) {
+              const G gv = gc[j0 + jj];
+#pragma unroll
+              for (int k = 0; k < RPT; ++k) {
+                const int r = tc + k * NCT;
+                if (r < rows) P::mac(acc[k], st[jj * rows + r], gv);
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) P::flush(acc[k]);
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[stg]);
+        }
+      }
+      if (failed) continue;
+      // block results
+      const int64_t s_out = d.lev < d.L ? out_seg_id(d, j, c) : 0;
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int r = tc + k * NCT;
+        if (r >= rows) continue;
+        const V v = P::fin(acc[k]);
+        if (d.kind == KIND_U) {
+          res[c * rcap + r] = v;
+        } else {
+          const V o = d.kind == KIND_V ? P::add(v, u[(c ? ix1 : ix0)[r]]) : v;
+          io.wout[d.out_off[s_out] + r] = o;
+        }
+      }
+      if (d.kind == KIND_V && cols == 0) {  // all skeleton: out = u[q]
+        for (int r = tc; r < rows; r += NCT) io.wout[d.out_off[s_out] + r] = u[(c ? ix1 : ix0)[r]];
+      }
+    }
+    if (failed) {
+      atomicOr(status, 1);
+      abort_flag = 1;
+      cons_abort = 1;
+    }
+    if (d.kind == KIND_U) {
+      consumer_sync();
+      if (*(volatile int*)&cons_abort) break;
+      const int tl = l0 + rows0;
+      for (int i = tc; i < l0; i += NCT) t[ix0[i]] = u[i];
+      for (int i = tc; i < rows0; i += NCT) t[ix0[l0 + i]] = res[i];
+      consumer_sync();
+      for (int i = tc; i < l1; i += NCT) { V* q = &t[ix1[i]]; *q = P::add(*q, u[l0 + i]); }
+      for (int i = tc; i < rows1; i += NCT) { V* q = &t[ix1[l1 + i]]; *q = P::add(*q, res[rcap + i]); }
+      consumer_sync();
+      if (d.lev == d.L) {
+        for (int i = tc; i < tl; i += NCT) io.y[j * d.n0 + i] = t[i];
+      } else {
+        const int64_t s0 = out_seg_id(d, j, 0), s1 = out_seg_id(d, j, 1);
+        const int len0 = d.out_len[s0];
+        const int64_t b0 = d.out_off[s0], b1 = d.out_off[s1];
+        for (int i = tc; i < tl; i += NCT) io.wout[i < len0 ? b0 + i : b1 + (i - len0)] = t[i];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 idbf_status ensure_workspace(Plan* p, int64_t nrhs) {
   const size_t need = (size_t)2 * p->max_seg_total * nrhs * 16;
   if (need <= p->ws_bytes) return IDBF_OK;
@@ -516,6 +787,21 @@ static idbf_status run_levels(Plan* p, const void* x, void* y, int64_t R, int64_
     const int gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
     const int rcap = std::max(li.max_rows, li.max_cols);
     dim3 grid((unsigned)p->m, (unsigned)((R + RB - 1) / RB));
+    if (!adjoint && RB == 1 && p->d_status && li.max_rows <= strm::RPT * strm::NCT &&
+        li.max_rows * (int)sizeof(typename P::mat_t) <= strm::STAGE_BYTES - 32) {
+      const strm::Geo geo = strm::geometry<P>(li.max_in, li.max_out, gcap, rcap);
+      if (geo.total <= 110 * 1024) {
+        IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_stream<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const unsigned ctas = (unsigned)std::min<int64_t>(p->m, 2 * (int64_t)sms);
+        k_level_stream<P><<<ctas, strm::NTHREADS, geo.total, st>>>(d, mat, io, gcap, rcap, li.max_in, li.max_out,
+                                                                   p->d_status, p->wait_limit_ns, p->producer_enabled);
+        IDBF_CUDA_TRY(cudaGetLastError());
+        continue;
+      }
+    }
     if (!adjoint) {
       const size_t sm = (size_t)RB * (li.max_in * sizeof(V) + 2 * gcap * sizeof(typename P::gv_t) +
                                       2 * rcap * sizeof(V) + li.max_out * sizeof(V));

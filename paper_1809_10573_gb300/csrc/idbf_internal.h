@@ -74,6 +74,9 @@ struct Plan {
   std::vector<void*> lmat[3];           // [format][L+1]
   std::vector<int32_t*> lidx;           // [L+1]
   void* d_ws = nullptr;
+  int* d_status = nullptr;              // device status word: bit 0 = a bounded wait timed out
+  uint64_t wait_limit_ns = 2000000000ull;  // limit of every device-side wait (2 s)
+  int producer_enabled = 1;             // 0 only in the timeout test (waits that nothing satisfies)
   size_t ws_bytes = 0;
   int rank_saturated = 0;
   double build_seconds = 0.0;

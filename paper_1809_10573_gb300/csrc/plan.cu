@@ -140,6 +140,10 @@ idbf_status upload_structure(Plan* p, cudaStream_t st) {
   IDBF_CUDA_TRY(cudaMemcpyAsync(p->d_rows, p->h_rows.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   IDBF_CUDA_TRY(cudaMemcpyAsync(p->d_cols, p->h_cols.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   IDBF_CUDA_TRY(cudaMemcpyAsync(p->d_seg_len, p->h_seg_len.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (!p->d_status) {
+    IDBF_CUDA_TRY(cudaMalloc((void**)&p->d_status, sizeof(int)));
+    IDBF_CUDA_TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
+  }
   return IDBF_OK;
 }
 
@@ -207,7 +211,7 @@ static idbf_status convert_level(Plan* p, int l, uint32_t mask, cudaStream_t st)
     const int g = conv_grid(n);
     if (want64 && !m[IDBF_STORE_C64]) {
       void* d = nullptr;
-      IDBF_CUDA_TRY(cudaMalloc(&d, n * sizeof(float2)));
+      IDBF_CUDA_TRY(cudaMalloc(&d, n * sizeof(float2) + 16));  // 16 B tail: bulk copies round up to 16 B
       if (has128) k_c128_to_c64<<<g, 256, 0, st>>>((const double2*)m[IDBF_STORE_C128], (float2*)d, n);
       else k_df64_to_c64<<<g, 256, 0, st>>>((const float4*)m[IDBF_STORE_DF64], (float2*)d, n);
       IDBF_CUDA_TRY(cudaGetLastError());
@@ -411,6 +415,29 @@ idbf_status idbf_set_storage(idbf_plan h, uint32_t mask, void* stream) {
   return convert_storage(&h->p, mask, (cudaStream_t)stream);
 }
 
+idbf_status idbf_sync_status(idbf_plan h, void* stream) {
+  if (!h) return IDBF_EINVAL;
+  Plan& p = h->p;
+  if (!p.d_status) return IDBF_OK;
+  int v = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  IDBF_CUDA_TRY(cudaMemcpyAsync(&v, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IDBF_CUDA_TRY(cudaStreamSynchronize(st));
+  if (v) {
+    IDBF_CUDA_TRY(cudaMemsetAsync(p.d_status, 0, sizeof(int), st));
+    IDBF_CUDA_TRY(cudaStreamSynchronize(st));
+    return IDBF_ETIMEOUT;
+  }
+  return IDBF_OK;
+}
+
+idbf_status idbf_debug_set_wait(idbf_plan h, uint64_t limit_ns, int32_t producer_enabled) {
+  if (!h || limit_ns == 0) return IDBF_EINVAL;
+  h->p.wait_limit_ns = limit_ns;
+  h->p.producer_enabled = producer_enabled ? 1 : 0;
+  return IDBF_OK;
+}
+
 idbf_status idbf_reserve(idbf_plan h, int64_t nrhs) {
   if (!h || nrhs < 1) return IDBF_EINVAL;
   return ensure_workspace(&h->p, nrhs);
@@ -546,6 +573,7 @@ void idbf_destroy(idbf_plan h) {
   for (int32_t* q : p.lidx) if (q) cudaFree(q);
   if (p.d_meta) cudaFree(p.d_meta);
   if (p.d_ws) cudaFree(p.d_ws);
+  if (p.d_status) cudaFree(p.d_status);
   if (cur != p.device) cudaSetDevice(cur);
   delete h;
 }
