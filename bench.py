@@ -355,7 +355,8 @@ def gpu_arm(args, rank, world, local):
             "e2e": {"value": e2e_value, "unit": "applies/s", "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
             "gpu_launches": (L + 1) * args.steps, "clocks": clocks, "modes": modes,
             "build": {"seconds": build_s, "entries": st["entries"], "levels": L + 1,
-                      "level_kmax": st["level_kmax"], "rank_saturated": st["rank_saturated"],
+                      "level_kmax": st["level_kmax"], "level_entries": st["level_entries"],
+                      "rank_saturated": st["rank_saturated"],
                       "device_GB": st["device_bytes"] / 1e9}}
     if rank == 0:
         print(json.dumps(line), flush=True)

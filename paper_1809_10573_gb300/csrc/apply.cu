@@ -487,9 +487,9 @@ namespace strm {
 constexpr int NCW = 6;
 constexpr int NCT = NCW * 32;
 constexpr int NTHREADS = NCT + 32;
-constexpr int STAGES = 3;
-constexpr int STAGE_BYTES = 24 * 1024;
-constexpr int RPT = 2;  // output rows per consumer thread: rows <= RPT * NCT
+constexpr int STAGES = 4;
+constexpr int STAGE_BYTES = 20 * 1024;
+constexpr int MAX_RPT = 2;  // output rows per consumer thread: rows <= MAX_RPT * NCT
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
@@ -541,26 +541,25 @@ __host__ __device__ __forceinline__ int cols_per_chunk(int rows, int es) {
 }
 
 struct Geo {
-  size_t vec_off, g_off, res_off, t_off, bar_off, total;
+  size_t vec_off, g_off, t_off, bar_off, total;
 };
 template <class P>
-__host__ __device__ inline Geo geometry(int max_in, int max_out, int gcap, int rcap) {
+__host__ __device__ inline Geo geometry(int max_in, int max_out, int gcap) {
   using V = typename P::vec_t;
   using G = typename P::gv_t;
   Geo q;
   q.vec_off = (size_t)STAGES * STAGE_BYTES;
   q.g_off = q.vec_off + (((size_t)max_in * sizeof(V) + 127) & ~(size_t)127);
-  q.res_off = q.g_off + (((size_t)2 * gcap * sizeof(G) + 127) & ~(size_t)127);
-  q.t_off = q.res_off + (((size_t)2 * rcap * sizeof(V) + 127) & ~(size_t)127);
+  q.t_off = q.g_off + (((size_t)2 * gcap * sizeof(G) + 127) & ~(size_t)127);
   q.bar_off = q.t_off + (((size_t)max_out * sizeof(V) + 127) & ~(size_t)127);
   q.total = q.bar_off + 2 * STAGES * sizeof(uint64_t);
   return q;
 }
 }  // namespace strm
 
-template <class P>
+template <class P, int RPT>
 __global__ void __launch_bounds__(strm::NTHREADS, 2)
-    k_level_stream(DevLevel d, const typename P::mat_t* __restrict__ mat, IO<typename P::vec_t> io, int gcap, int rcap,
+    k_level_stream(DevLevel d, const typename P::mat_t* __restrict__ mat, IO<typename P::vec_t> io, int gcap,
                    int max_in, int max_out, int* __restrict__ status, uint64_t limit_ns, int producer_enabled) {
   using namespace strm;
   using V = typename P::vec_t;
@@ -568,11 +567,10 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)
   using M = typename P::mat_t;
   constexpr int ES = (int)sizeof(M);
   extern __shared__ __align__(128) unsigned char smem[];
-  const Geo geo = geometry<P>(max_in, max_out, gcap, rcap);
+  const Geo geo = geometry<P>(max_in, max_out, gcap);
   unsigned char* stages = smem;
   V* u = (V*)(smem + geo.vec_off);
   G* g = (G*)(smem + geo.g_off);
-  V* res = (V*)(smem + geo.res_off);
   V* t = (V*)(smem + geo.t_off);
   uint64_t* full = (uint64_t*)(smem + geo.bar_off);
   uint64_t* empty = full + STAGES;
@@ -666,9 +664,19 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)
     }
     consumer_sync();
     bool failed = false;
+    const int tl = l0 + rows0;  // row-ID levels: |t| = |q_0| + |p_0|
+    if (d.kind == KIND_U) {
+      // t[q_0] = in_0 now; t[p_0] is written by the block-0 products below (q_0, p_0 partition t)
+      for (int i = tc; i < l0; i += NCT) t[ix0[i]] = u[i];
+    }
     for (int c = 0; c < 2; ++c) {
       const int rows = c ? rows1 : rows0, cols = c ? cols1 : cols0;
+      const int32_t* ix = c ? ix1 : ix0;
       const G* gc = g + (d.kind == KIND_S ? 0 : c * gcap);
+      if (d.kind == KIND_U && c == 1) {
+        consumer_sync();  // block 0 has written all of t
+        for (int i = tc; i < l1; i += NCT) { V* q = &t[ix1[i]]; *q = P::add(*q, u[l0 + i]); }
+      }
       typename P::acc_t acc[RPT];
 #pragma unroll
       for (int k = 0; k < RPT; ++k) P::init(acc[k]);
@@ -682,25 +690,30 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)
           if (!failed) {
             const uintptr_t src = base + (uintptr_t)j0 * rows * ES;
             const int shift = (int)((src & 15) / ES);
-            const M* st = (const M*)(stages + (size_t)stg * STAGE_BYTES) + shift;
+            const M* st = (const M*)(stages + (size_t)stg * STAGE_BYTES) + shift + tc;
+            if (RPT == 1) {
+              if (tc < rows) {
 #pragma unroll 4
-            for (int jj = 0; jj < nc; ++jj) {
-              const G gv = gc[j0 + jj];
-#pragma unroll
-              for (int k = 0; k < RPT; ++k) {
-                const int r = tc + k * NCT;
-                if (r < rows) P::mac(acc[k], st[jj * rows + r], gv);
+                for (int jj = 0; jj < nc; ++jj) P::mac(acc[0], st[jj * rows], gc[j0 + jj]);
+                P::flush(acc[0]);
               }
-            }
+            } else {
+#pragma unroll 2
+              for (int jj = 0; jj < nc; ++jj) {
+                const G gv = gc[j0 + jj];
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) P::flush(acc[k]);
+                for (int k = 0; k < RPT; ++k)
+                  if (tc + k * NCT < rows) P::mac(acc[k], st[jj * rows + k * NCT], gv);
+              }
+#pragma unroll
+              for (int k = 0; k < RPT; ++k) P::flush(acc[k]);
+            }
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[stg]);
         }
       }
       if (failed) continue;
-      // block results
       const int64_t s_out = d.lev < d.L ? out_seg_id(d, j, c) : 0;
 #pragma unroll
       for (int k = 0; k < RPT; ++k) {
@@ -708,14 +721,14 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)
         if (r >= rows) continue;
         const V v = P::fin(acc[k]);
         if (d.kind == KIND_U) {
-          res[c * rcap + r] = v;
+          V* q = &t[ix[l0 * (1 - c) + l1 * c + r]];
+          *q = c ? P::add(*q, v) : v;
         } else {
-          const V o = d.kind == KIND_V ? P::add(v, u[(c ? ix1 : ix0)[r]]) : v;
-          io.wout[d.out_off[s_out] + r] = o;
+          io.wout[d.out_off[s_out] + r] = d.kind == KIND_V ? P::add(v, u[ix[r]]) : v;
         }
       }
       if (d.kind == KIND_V && cols == 0) {  // all skeleton: out = u[q]
-        for (int r = tc; r < rows; r += NCT) io.wout[d.out_off[s_out] + r] = u[(c ? ix1 : ix0)[r]];
+        for (int r = tc; r < rows; r += NCT) io.wout[d.out_off[s_out] + r] = u[ix[r]];
       }
     }
     if (failed) {
@@ -726,13 +739,6 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)
     if (d.kind == KIND_U) {
       consumer_sync();
       if (*(volatile int*)&cons_abort) break;
-      const int tl = l0 + rows0;
-      for (int i = tc; i < l0; i += NCT) t[ix0[i]] = u[i];
-      for (int i = tc; i < rows0; i += NCT) t[ix0[l0 + i]] = res[i];
-      consumer_sync();
-      for (int i = tc; i < l1; i += NCT) { V* q = &t[ix1[i]]; *q = P::add(*q, u[l0 + i]); }
-      for (int i = tc; i < rows1; i += NCT) { V* q = &t[ix1[l1 + i]]; *q = P::add(*q, res[rcap + i]); }
-      consumer_sync();
       if (d.lev == d.L) {
         for (int i = tc; i < tl; i += NCT) io.y[j * d.n0 + i] = t[i];
       } else {
@@ -787,17 +793,25 @@ static idbf_status run_levels(Plan* p, const void* x, void* y, int64_t R, int64_
     const int gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
     const int rcap = std::max(li.max_rows, li.max_cols);
     dim3 grid((unsigned)p->m, (unsigned)((R + RB - 1) / RB));
-    if (!adjoint && RB == 1 && p->d_status && li.max_rows <= strm::RPT * strm::NCT &&
+    // one right-hand side, forward, FP32-pair or FP32 arithmetic: the streaming kernel (FP64 FMA
+    // is bound by the FP64 pipe and runs faster in the per-node kernel, which keeps more warps)
+    if (!adjoint && RB == 1 && p->d_status && fmt != IDBF_STORE_C128 && li.max_rows <= strm::MAX_RPT * strm::NCT &&
         li.max_rows * (int)sizeof(typename P::mat_t) <= strm::STAGE_BYTES - 32) {
-      const strm::Geo geo = strm::geometry<P>(li.max_in, li.max_out, gcap, rcap);
-      if (geo.total <= 110 * 1024) {
-        IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_stream<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
+      const strm::Geo geo = strm::geometry<P>(li.max_in, li.max_out, gcap);
+      if (geo.total <= 112 * 1024) {
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const unsigned ctas = (unsigned)std::min<int64_t>(p->m, 2 * (int64_t)sms);
-        k_level_stream<P><<<ctas, strm::NTHREADS, geo.total, st>>>(d, mat, io, gcap, rcap, li.max_in, li.max_out,
-                                                                   p->d_status, p->wait_limit_ns, p->producer_enabled);
+        if (li.max_rows <= strm::NCT) {
+          IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_stream<P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
+          k_level_stream<P, 1><<<ctas, strm::NTHREADS, geo.total, st>>>(d, mat, io, gcap, li.max_in, li.max_out,
+                                                                        p->d_status, p->wait_limit_ns, p->producer_enabled);
+        } else {
+          IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_stream<P, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
+          k_level_stream<P, 2><<<ctas, strm::NTHREADS, geo.total, st>>>(d, mat, io, gcap, li.max_in, li.max_out,
+                                                                        p->d_status, p->wait_limit_ns, p->producer_enabled);
+        }
         IDBF_CUDA_TRY(cudaGetLastError());
         continue;
       }

@@ -123,16 +123,16 @@ def test_bounded_waits_report_a_timeout_and_the_context_survives():
     # runs out after 20 ms; the kernels must return, the host must read ETIMEOUT, and the next
     # apply on the same context must be exact again
     from paper_1809_10573_gb300 import _lib
-    c, plan = _plan("fio_base_4096")
+    c, plan = _plan("fio_base_4096", P.STORE_DF64)
     L = _lib.lib()
     X = inputs.complex_gaussian(c["N"], 1, seed=31)
     xd = torch.from_numpy(X).cuda()
     assert L.idbf_debug_set_wait(plan._h, 20_000_000, 0) == _lib.OK
-    plan.apply(xd, mode=P.MODE_FP64)
+    plan.apply(xd, mode=P.MODE_DF64)   # one right-hand side: the streaming kernel
     with pytest.raises(P.IDBFError) as err:
         plan.sync_status()
     assert err.value.status == _lib.ETIMEOUT
     assert L.idbf_debug_set_wait(plan._h, 2_000_000_000, 1) == _lib.OK
-    y = plan.apply(xd, mode=P.MODE_FP64)
+    y = plan.apply(xd, mode=P.MODE_DF64)
     plan.sync_status()
     assert rel(y.cpu().numpy(), idbf.apply(c["F"], X)) < 1e-12
