@@ -57,6 +57,9 @@ struct FP64P {
   }
   __device__ static __forceinline__ vec_t add(vec_t a, vec_t b) { return make_double2(a.x + b.x, a.y + b.y); }
   __device__ static __forceinline__ vec_t zero() { return make_double2(0.0, 0.0); }
+  using part_t = double2;  // a flushed accumulator, for combining partial sums
+  __device__ static __forceinline__ part_t part(const acc_t& a) { return make_double2(a.re, a.im); }
+  __device__ static __forceinline__ void combine(acc_t& a, const part_t& b) { a.re += b.x; a.im += b.y; }
 };
 
 struct FP32P {
@@ -91,6 +94,9 @@ struct FP32P {
   }
   __device__ static __forceinline__ vec_t add(vec_t a, vec_t b) { return make_float2(a.x + b.x, a.y + b.y); }
   __device__ static __forceinline__ vec_t zero() { return make_float2(0.f, 0.f); }
+  using part_t = float2;
+  __device__ static __forceinline__ part_t part(const acc_t& a) { return make_float2(a.re, a.im); }
+  __device__ static __forceinline__ void combine(acc_t& a, const part_t& b) { a.re += b.x; a.im += b.y; }
 };
 
 // ---- double-float helpers (round-to-nearest intrinsics: never contracted into FMA) ----------
@@ -172,6 +178,12 @@ struct DF64P {
   }
   __device__ static __forceinline__ vec_t add(vec_t a, vec_t b) { return make_double2(a.x + b.x, a.y + b.y); }
   __device__ static __forceinline__ vec_t zero() { return make_double2(0.0, 0.0); }
+  using part_t = float4;  // (re_hi, re_lo, im_hi, im_lo) of a flushed accumulator
+  __device__ static __forceinline__ part_t part(const acc_t& a) { return make_float4(a.hr, a.lr, a.hi, a.li); }
+  __device__ static __forceinline__ void combine(acc_t& a, const part_t& b) {
+    dw_accumulate(a.hr, a.lr, b.x, b.y);
+    dw_accumulate(a.hi, a.li, b.z, b.w);
+  }
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -484,12 +496,15 @@ __global__ void __launch_bounds__(256) k_level_adj(DevLevel d, const typename P:
 // Every wait is bounded (globaltimer): on a timeout the CTA sets bit 0 of *status, lets its
 // copies in flight land, and leaves; the host reads the status with idbf_sync_status.
 namespace strm {
-constexpr int NCW = 6;
+constexpr int TEAMS = 2;                 // consumer teams; team k takes chunks k, k+2, ... of a block
+constexpr int TCW = 6;                   // warps per team
+constexpr int TCT = TCW * 32;            // threads per team (one output row each)
+constexpr int NCW = TEAMS * TCW;
 constexpr int NCT = NCW * 32;
 constexpr int NTHREADS = NCT + 32;
 constexpr int STAGES = 4;
 constexpr int STAGE_BYTES = 20 * 1024;
-constexpr int MAX_RPT = 2;  // output rows per consumer thread: rows <= MAX_RPT * NCT
+constexpr int MAX_RPT = 2;  // output rows per team thread: rows <= MAX_RPT * TCT
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
@@ -541,7 +556,7 @@ __host__ __device__ __forceinline__ int cols_per_chunk(int rows, int es) {
 }
 
 struct Geo {
-  size_t vec_off, g_off, t_off, bar_off, total;
+  size_t vec_off, g_off, t_off, red_off, bar_off, total;
 };
 template <class P>
 __host__ __device__ inline Geo geometry(int max_in, int max_out, int gcap) {
@@ -551,14 +566,15 @@ __host__ __device__ inline Geo geometry(int max_in, int max_out, int gcap) {
   q.vec_off = (size_t)STAGES * STAGE_BYTES;
   q.g_off = q.vec_off + (((size_t)max_in * sizeof(V) + 127) & ~(size_t)127);
   q.t_off = q.g_off + (((size_t)2 * gcap * sizeof(G) + 127) & ~(size_t)127);
-  q.bar_off = q.t_off + (((size_t)max_out * sizeof(V) + 127) & ~(size_t)127);
+  q.red_off = q.t_off + (((size_t)max_out * sizeof(V) + 127) & ~(size_t)127);
+  q.bar_off = q.red_off + (((size_t)MAX_RPT * TCT * sizeof(typename P::part_t) + 127) & ~(size_t)127);
   q.total = q.bar_off + 2 * STAGES * sizeof(uint64_t);
   return q;
 }
 }  // namespace strm
 
 template <class P, int RPT>
-__global__ void __launch_bounds__(strm::NTHREADS, 2)
+__global__ void __launch_bounds__(strm::NTHREADS, 2)  // two CTAs (26 warps) per SM
     k_level_stream(DevLevel d, const typename P::mat_t* __restrict__ mat, IO<typename P::vec_t> io, int gcap,
                    int max_in, int max_out, int* __restrict__ status, uint64_t limit_ns, int producer_enabled) {
   using namespace strm;
@@ -572,6 +588,7 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)
   V* u = (V*)(smem + geo.vec_off);
   G* g = (G*)(smem + geo.g_off);
   V* t = (V*)(smem + geo.t_off);
+  typename P::part_t* red = (typename P::part_t*)(smem + geo.red_off);
   uint64_t* full = (uint64_t*)(smem + geo.bar_off);
   uint64_t* empty = full + STAGES;
   // abort_flag: any warp, only shortens waits. cons_abort: written by consumers before a
@@ -582,7 +599,7 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], NCW);
+      mbar_init(&empty[i], TCW);  // a stage is consumed by the warps of one team
     }
     abort_flag = 0;
     cons_abort = 0;
@@ -631,9 +648,9 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)
   }
 
   // ---------------- consumers ----------------
-  const int tc = threadIdx.x - 32;
-  const int cw = warp - 1;
-  (void)cw;
+  const int tc = threadIdx.x - 32;      // 0 .. NCT-1: prologue / epilogue index
+  const int team = tc / TCT;
+  const int tr = tc - team * TCT;       // row index within the team
   uint32_t it = 0;
   for (int64_t j = blockIdx.x; j < d.m; j += gridDim.x) {
     consumer_sync();
@@ -673,26 +690,28 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)
       const int rows = c ? rows1 : rows0, cols = c ? cols1 : cols0;
       const int32_t* ix = c ? ix1 : ix0;
       const G* gc = g + (d.kind == KIND_S ? 0 : c * gcap);
-      if (d.kind == KIND_U && c == 1) {
-        consumer_sync();  // block 0 has written all of t
+      if (d.kind == KIND_U && c == 1) {  // block 0 has written all of t (end-of-block sync)
         for (int i = tc; i < l1; i += NCT) { V* q = &t[ix1[i]]; *q = P::add(*q, u[l0 + i]); }
       }
       typename P::acc_t acc[RPT];
 #pragma unroll
       for (int k = 0; k < RPT; ++k) P::init(acc[k]);
-      if (rows > 0 && cols > 0) {
+      const bool work = rows > 0 && cols > 0;
+      if (work) {
         const int cpc = cols_per_chunk(rows, ES);
         const uintptr_t base = (uintptr_t)(mat + d.moff[2 * j + c]);
-        for (int j0 = 0; j0 < cols; j0 += cpc, ++it) {
+        int ch = 0;
+        for (int j0 = 0; j0 < cols; j0 += cpc, ++it, ++ch) {
+          if ((ch & (TEAMS - 1)) != team) continue;  // the other team's chunk
           const int nc = min(cpc, cols - j0);
           const int stg = it % STAGES;
           if (!failed && !wait_bounded(&full[stg], (it / STAGES) & 1, limit_ns, &abort_flag)) failed = true;
           if (!failed) {
             const uintptr_t src = base + (uintptr_t)j0 * rows * ES;
             const int shift = (int)((src & 15) / ES);
-            const M* st = (const M*)(stages + (size_t)stg * STAGE_BYTES) + shift + tc;
+            const M* st = (const M*)(stages + (size_t)stg * STAGE_BYTES) + shift + tr;
             if (RPT == 1) {
-              if (tc < rows) {
+              if (tr < rows) {
 #pragma unroll 4
                 for (int jj = 0; jj < nc; ++jj) P::mac(acc[0], st[jj * rows], gc[j0 + jj]);
                 P::flush(acc[0]);
@@ -703,7 +722,7 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)
                 const G gv = gc[j0 + jj];
 #pragma unroll
                 for (int k = 0; k < RPT; ++k)
-                  if (tc + k * NCT < rows) P::mac(acc[k], st[jj * rows + k * NCT], gv);
+                  if (tr + k * TCT < rows) P::mac(acc[k], st[jj * rows + k * TCT], gv);
               }
 #pragma unroll
               for (int k = 0; k < RPT; ++k) P::flush(acc[k]);
@@ -712,24 +731,39 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[stg]);
         }
-      }
-      if (failed) continue;
-      const int64_t s_out = d.lev < d.L ? out_seg_id(d, j, c) : 0;
+        // team 1 hands its partial sums to team 0
+        if (team == 1) {
 #pragma unroll
-      for (int k = 0; k < RPT; ++k) {
-        const int r = tc + k * NCT;
-        if (r >= rows) continue;
-        const V v = P::fin(acc[k]);
-        if (d.kind == KIND_U) {
-          V* q = &t[ix[l0 * (1 - c) + l1 * c + r]];
-          *q = c ? P::add(*q, v) : v;
-        } else {
-          io.wout[d.out_off[s_out] + r] = d.kind == KIND_V ? P::add(v, u[ix[r]]) : v;
+          for (int k = 0; k < RPT; ++k)
+            if (tr + k * TCT < rows) red[k * TCT + tr] = P::part(acc[k]);
         }
       }
-      if (d.kind == KIND_V && cols == 0) {  // all skeleton: out = u[q]
+      consumer_sync();
+      if (work && team == 0) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+          if (tr + k * TCT < rows) P::combine(acc[k], red[k * TCT + tr]);
+      }
+      // no early exit here: every consumer warp must reach the barrier at the end of the block
+      const int64_t s_out = d.lev < d.L ? out_seg_id(d, j, c) : 0;
+      if (team == 0 && !failed) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+          const int r = tr + k * TCT;
+          if (r >= rows) continue;
+          const V v = P::fin(acc[k]);
+          if (d.kind == KIND_U) {
+            V* q = &t[ix[l0 * (1 - c) + l1 * c + r]];
+            *q = c ? P::add(*q, v) : v;
+          } else {
+            io.wout[d.out_off[s_out] + r] = d.kind == KIND_V ? P::add(v, u[ix[r]]) : v;
+          }
+        }
+      }
+      if (d.kind == KIND_V && cols == 0 && !failed) {  // all skeleton: out = u[q]
         for (int r = tc; r < rows; r += NCT) io.wout[d.out_off[s_out] + r] = u[ix[r]];
       }
+      consumer_sync();  // red is reused by the next block; t must be complete before c = 1
     }
     if (failed) {
       atomicOr(status, 1);
@@ -795,7 +829,7 @@ static idbf_status run_levels(Plan* p, const void* x, void* y, int64_t R, int64_
     dim3 grid((unsigned)p->m, (unsigned)((R + RB - 1) / RB));
     // one right-hand side, forward, FP32-pair or FP32 arithmetic: the streaming kernel (FP64 FMA
     // is bound by the FP64 pipe and runs faster in the per-node kernel, which keeps more warps)
-    if (!adjoint && RB == 1 && p->d_status && fmt != IDBF_STORE_C128 && li.max_rows <= strm::MAX_RPT * strm::NCT &&
+    if (!adjoint && RB == 1 && p->d_status && fmt != IDBF_STORE_C128 && li.max_rows <= strm::MAX_RPT * strm::TCT &&
         li.max_rows * (int)sizeof(typename P::mat_t) <= strm::STAGE_BYTES - 32) {
       const strm::Geo geo = strm::geometry<P>(li.max_in, li.max_out, gcap);
       if (geo.total <= 112 * 1024) {
@@ -803,7 +837,7 @@ static idbf_status run_levels(Plan* p, const void* x, void* y, int64_t R, int64_
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const unsigned ctas = (unsigned)std::min<int64_t>(p->m, 2 * (int64_t)sms);
-        if (li.max_rows <= strm::NCT) {
+        if (li.max_rows <= strm::TCT) {
           IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_stream<P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
           k_level_stream<P, 1><<<ctas, strm::NTHREADS, geo.total, st>>>(d, mat, io, gcap, li.max_in, li.max_out,
                                                                         p->d_status, p->wait_limit_ns, p->producer_enabled);
