@@ -276,6 +276,14 @@ def gpu_arm(args, rank, world, local):
     rel_32 = float(torch.linalg.norm(y32.to(torch.complex128) - y64) / nrm) if "fp32" in want else None
     plan.set_storage(*fmts_final)
 
+    # autotuner: fastest forward kernel per level for each timed mode (untimed)
+    tune = {}
+    for name, mode in (("df64", P.MODE_DF64), ("fp32", P.MODE_FP32)):
+        if name in want:
+            ms_sum = plan.autotune(mode, reps=3)
+            fmt = P.STORE_DF64 if name == "df64" else P.STORE_C64
+            tune[name] = {"level_variants": plan.stats()["level_variant"][fmt], "sum_of_level_ms": ms_sum}
+
     def timed(mode, vec, steps, warmup, sampler_index=None):
         for _ in range(warmup):
             plan.apply(vec, mode=mode, out=ybuf[mode])
@@ -353,7 +361,7 @@ def gpu_arm(args, rank, world, local):
             "rel_err": {"eps_a_fp64_vs_dense_256_rows": eps_a, "df64_vs_fp64": rel_df, "fp32_vs_fp64": rel_32},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "applies/s", "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
-            "gpu_launches": (L + 1) * args.steps, "clocks": clocks, "modes": modes,
+            "gpu_launches": (L + 1) * args.steps, "clocks": clocks, "modes": modes, "autotune": tune,
             "build": {"seconds": build_s, "entries": st["entries"], "levels": L + 1,
                       "level_kmax": st["level_kmax"], "level_entries": st["level_entries"],
                       "rank_saturated": st["rank_saturated"],

@@ -134,6 +134,16 @@ class Plan:
         return _lib.check(fn(self._h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), nrhs, ld, mode, C.c_void_p(stream_ptr)),
                           fn.__name__)
 
+    def autotune(self, mode=MODE_DF64, reps=3, stream=None) -> float:
+        """Pick the fastest forward kernel per level for `mode`; returns the summed level times (ms)."""
+        ms = C.c_float()
+        _lib.check(_lib.lib().idbf_autotune(self._h, mode, reps, _stream_ptr(stream), C.byref(ms)), "idbf_autotune")
+        return ms.value
+
+    def set_level_variants(self, mode, variants):
+        arr = (C.c_int32 * len(variants))(*variants)
+        _lib.check(_lib.lib().idbf_set_level_variants(self._h, mode, arr, len(variants)), "idbf_set_level_variants")
+
     def sync_status(self, stream=None):
         """Wait for the stream; raise IDBFError(ETIMEOUT) if a device-side wait gave up."""
         _lib.check(_lib.lib().idbf_sync_status(self._h, _stream_ptr(stream)), "idbf_sync_status")
@@ -155,7 +165,8 @@ class Plan:
                     rank_saturated=s.rank_saturated, entries=s.entries, index_entries=s.index_entries,
                     level_entries=list(s.level_entries[:nl]), level_kmin=list(s.level_kmin[:nl]),
                     level_kmax=list(s.level_kmax[:nl]), segment_entries=s.segment_entries,
-                    build_seconds=s.build_seconds, device_bytes=s.device_bytes)
+                    build_seconds=s.build_seconds, device_bytes=s.device_bytes,
+                    level_variant={f: list(s.level_variant[f][:nl]) for f in range(3)})
 
     def algorithmic_bytes(self, nrhs: int = 1, entry_bytes: int = 16, vec_bytes: int = 16) -> int:
         """Bytes one apply must move at least: every stored factor entry once, the int32

@@ -43,7 +43,8 @@ class Stats(C.Structure):
                 ("entries", C.c_int64), ("index_entries", C.c_int64),
                 ("level_entries", C.c_int64 * MAX_LEVELS), ("level_kmin", C.c_int32 * MAX_LEVELS),
                 ("level_kmax", C.c_int32 * MAX_LEVELS), ("segment_entries", C.c_int64),
-                ("build_seconds", C.c_double), ("device_bytes", C.c_int64)]
+                ("build_seconds", C.c_double), ("device_bytes", C.c_int64),
+                ("level_variant", (C.c_int32 * MAX_LEVELS) * 3)]
 
 
 _lib = None
@@ -61,6 +62,8 @@ SIGNATURES = {
                                      C.c_void_p]),
     "idbf_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
                                      C.c_void_p]),
+    "idbf_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_float)]),
+    "idbf_set_level_variants": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
     "idbf_reserve": (C.c_int, [C.c_void_p, C.c_int64]),
     "idbf_sync_status": (C.c_int, [C.c_void_p, C.c_void_p]),
     "idbf_debug_set_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32]),

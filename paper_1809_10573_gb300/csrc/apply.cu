@@ -186,6 +186,11 @@ struct DF64P {
   }
 };
 
+template <class P> constexpr int fmt_of();
+template <> constexpr int fmt_of<FP64P>() { return IDBF_STORE_C128; }
+template <> constexpr int fmt_of<DF64P>() { return IDBF_STORE_DF64; }
+template <> constexpr int fmt_of<FP32P>() { return IDBF_STORE_C64; }
+
 // ---------------------------------------------------------------------------------------------
 // addressing of a node's input and output segments
 struct Seg {
@@ -496,15 +501,31 @@ __global__ void __launch_bounds__(256) k_level_adj(DevLevel d, const typename P:
 // Every wait is bounded (globaltimer): on a timeout the CTA sets bit 0 of *status, lets its
 // copies in flight land, and leaves; the host reads the status with idbf_sync_status.
 namespace strm {
-constexpr int TEAMS = 2;                 // consumer teams; team k takes chunks k, k+2, ... of a block
-constexpr int TCW = 6;                   // warps per team
+constexpr int TCW = 6;                   // warps per consumer team
 constexpr int TCT = TCW * 32;            // threads per team (one output row each)
-constexpr int NCW = TEAMS * TCW;
-constexpr int NCT = NCW * 32;
-constexpr int NTHREADS = NCT + 32;
-constexpr int STAGES = 4;
-constexpr int STAGE_BYTES = 20 * 1024;
-constexpr int MAX_RPT = 2;  // output rows per team thread: rows <= MAX_RPT * TCT
+constexpr int MAX_RPT = 2;               // output rows per team thread: rows <= MAX_RPT * TCT
+constexpr int FLUSH_TERMS = 16;          // double-float partial sums are folded after >= 16 terms
+// Ring of stages and team layout per arithmetic. Chunk i (counted over the whole launch) goes to
+// stage i % STAGES and to team i % TEAMS, so with STAGES a multiple of TEAMS every stage is read
+// by one team only, and a team never waits for a phase of a stage more than one phase ahead of
+// the last one it consumed there (an mbarrier parity wait cannot tell phase k from k + 2).
+//   double-float: issue bound, so one CTA per SM with four teams and large stages;
+//   FP32: memory-latency bound, two CTAs per SM with two teams each.
+struct RingA {  // two CTAs per SM, two teams each
+  static constexpr int TEAMS = 2, STAGES = 4, STAGE_BYTES = 18 * 1024, CTAS = 2;
+  static constexpr int NCT = TEAMS * TCT, NTHREADS = NCT + 32;
+};
+struct RingB {  // two CTAs per SM, one team each, fewer and larger stages
+  static constexpr int TEAMS = 1, STAGES = 3, STAGE_BYTES = 24 * 1024, CTAS = 2;
+  static constexpr int NCT = TEAMS * TCT, NTHREADS = NCT + 32;
+};
+struct RingC {  // one CTA per SM, four teams, eight stages
+  static constexpr int TEAMS = 4, STAGES = 8, STAGE_BYTES = 22 * 1024, CTAS = 1;
+  static constexpr int NCT = TEAMS * TCT, NTHREADS = NCT + 32;
+};
+static_assert(RingA::STAGES % RingA::TEAMS == 0 && RingB::STAGES % RingB::TEAMS == 0 &&
+                  RingC::STAGES % RingC::TEAMS == 0,
+              "every stage must belong to one team");
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
@@ -535,62 +556,82 @@ __device__ __forceinline__ uint64_t gtimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+template <int NCT>
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NCT) : "memory"); }
 
 // Wait until phase `parity` of barrier b has completed, giving up after limit_ns or when
-// another warp has flagged an abort.
+// another warp has flagged an abort. The timer and the flag are read every 256 polls only, so
+// that a waiting warp takes few issue slots from the warps that compute.
 __device__ __forceinline__ bool wait_bounded(uint64_t* b, uint32_t parity, uint64_t limit_ns, volatile int* abort_flag) {
   if (mbar_try_wait(b, parity)) return true;
   const uint64_t t0 = gtimer();
-  while (!mbar_try_wait(b, parity)) {
-    if (*abort_flag || gtimer() - t0 > limit_ns) return false;
+  for (uint32_t n = 1;; ++n) {
+    if (mbar_try_wait(b, parity)) return true;
+    if ((n & 255) == 0 && (*abort_flag || gtimer() - t0 > limit_ns)) return false;
   }
-  return true;
 }
 
 // columns per chunk for a block with `rows` rows and elements of es bytes; 8-byte elements may
 // start 8 bytes past a 16-byte boundary, which costs up to two elements of slack
-__host__ __device__ __forceinline__ int cols_per_chunk(int rows, int es) {
-  const int cap = STAGE_BYTES / es - (es == 8 ? 2 : 0);
+__host__ __device__ __forceinline__ int cols_per_chunk(int rows, int es, int stage_bytes) {
+  const int cap = stage_bytes / es - (es == 8 ? 2 : 0);
   return max(1, cap / max(rows, 1));
 }
 
 struct Geo {
-  size_t vec_off, g_off, t_off, red_off, bar_off, total;
+  size_t vec_off, ibuf_off, g_off, t_off, red_off, bar_off, total;
+  int ucap, icap;  // elements of one input buffer, ints of one index buffer
 };
-template <class P>
-__host__ __device__ inline Geo geometry(int max_in, int max_out, int gcap) {
+// Shared memory: the stage ring, two input buffers (node inputs, copied by the producer), two
+// index buffers (q and p lists of both blocks), the gathered operands, the row-ID accumulator t,
+// the team reduction buffer and the mbarriers.
+template <class P, class RG>
+__host__ __device__ inline Geo geometry(int max_in, int max_out, int max_cols_pair, int rpt) {
   using V = typename P::vec_t;
   using G = typename P::gv_t;
+  constexpr int STAGES = RG::STAGES, STAGE_BYTES = RG::STAGE_BYTES;
   Geo q;
+  // capacities rounded to 16 bytes so that buffer 1 starts 16-byte aligned (bulk-copy destination);
+  // + room for a start shifted within 16 bytes and a length rounded up to 16 bytes
+  q.ucap = (max_in + 16 / (int)sizeof(V) + 1 + 3) & ~3;
+  q.icap = (2 * (max_in > max_out ? max_in : max_out) + 16 + 3) & ~3;
+  const int gsz = max_cols_pair > max_in ? max_cols_pair : max_in;
   q.vec_off = (size_t)STAGES * STAGE_BYTES;
-  q.g_off = q.vec_off + (((size_t)max_in * sizeof(V) + 127) & ~(size_t)127);
-  q.t_off = q.g_off + (((size_t)2 * gcap * sizeof(G) + 127) & ~(size_t)127);
+  q.ibuf_off = q.vec_off + ((2 * (size_t)q.ucap * sizeof(V) + 127) & ~(size_t)127);
+  q.g_off = q.ibuf_off + ((2 * (size_t)q.icap * sizeof(int32_t) + 127) & ~(size_t)127);
+  q.t_off = q.g_off + (((size_t)gsz * sizeof(G) + 127) & ~(size_t)127);
   q.red_off = q.t_off + (((size_t)max_out * sizeof(V) + 127) & ~(size_t)127);
-  q.bar_off = q.red_off + (((size_t)MAX_RPT * TCT * sizeof(typename P::part_t) + 127) & ~(size_t)127);
-  q.total = q.bar_off + 2 * STAGES * sizeof(uint64_t);
+  q.bar_off = q.red_off + (((size_t)(RG::TEAMS > 1 ? RG::TEAMS - 1 : 1) * rpt * TCT * sizeof(typename P::part_t) + 127) & ~(size_t)127);
+  q.total = q.bar_off + 4 * STAGES * sizeof(uint64_t);
   return q;
 }
 }  // namespace strm
 
-template <class P, int RPT>
-__global__ void __launch_bounds__(strm::NTHREADS, 2)  // two CTAs (26 warps) per SM
-    k_level_stream(DevLevel d, const typename P::mat_t* __restrict__ mat, IO<typename P::vec_t> io, int gcap,
-                   int max_in, int max_out, int* __restrict__ status, uint64_t limit_ns, int producer_enabled) {
+template <class P, class RG, int RPT>
+__global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
+    k_level_stream(DevLevel d, const typename P::mat_t* __restrict__ mat, IO<typename P::vec_t> io, int max_in,
+                   int max_out, int max_cols_pair, int x_bulk, int* __restrict__ status, uint64_t limit_ns,
+                   int producer_enabled) {
   using namespace strm;
   using V = typename P::vec_t;
   using G = typename P::gv_t;
   using M = typename P::mat_t;
   constexpr int ES = (int)sizeof(M);
+  constexpr int VS = (int)sizeof(V);
+  constexpr int STAGES = RG::STAGES, STAGE_BYTES = RG::STAGE_BYTES;
+  constexpr int TEAMS = RG::TEAMS, NCT = RG::NCT;
   extern __shared__ __align__(128) unsigned char smem[];
-  const Geo geo = geometry<P>(max_in, max_out, gcap);
+  const Geo geo = geometry<P, RG>(max_in, max_out, max_cols_pair, RPT);
   unsigned char* stages = smem;
-  V* u = (V*)(smem + geo.vec_off);
+  V* ubuf = (V*)(smem + geo.vec_off);              // [2][ucap]
+  int32_t* ibuf = (int32_t*)(smem + geo.ibuf_off);  // [2][icap]
   G* g = (G*)(smem + geo.g_off);
   V* t = (V*)(smem + geo.t_off);
   typename P::part_t* red = (typename P::part_t*)(smem + geo.red_off);
   uint64_t* full = (uint64_t*)(smem + geo.bar_off);
   uint64_t* empty = full + STAGES;
+  uint64_t* in_full = empty + STAGES;   // [2]
+  uint64_t* in_empty = in_full + 2;     // [2]
   // abort_flag: any warp, only shortens waits. cons_abort: written by consumers before a
   // consumer barrier and read after it, so that all consumer warps leave the loop together.
   __shared__ int abort_flag;
@@ -599,24 +640,61 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)  // two CTAs (26 warps) per
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], TCW);  // a stage is consumed by the warps of one team
+      mbar_init(&empty[i], strm::TCW);  // a stage is consumed by the warps of one team
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&in_full[i], 1);
+      mbar_init(&in_empty[i], 1);
     }
     abort_flag = 0;
     cons_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  const bool inputs_bulk = x_bulk != 0;  // producer copies node inputs (else consumers load them)
 
   if (warp == 0) {
     // ---------------- producer ----------------
     if (lane != 0) return;
-    uint32_t it = 0;
+    uint32_t it = 0, nn = 0;
     bool ok = true;
-    for (int64_t j = blockIdx.x; j < d.m && ok; j += gridDim.x) {
+    for (int64_t j = blockIdx.x; j < d.m && ok; j += gridDim.x, ++nn) {
+      // node inputs and index lists into buffer nn & 1 (released by the consumers of node nn-2)
+      const int b = nn & 1;
+      if (!wait_bounded(&in_empty[b], ((nn >> 1) & 1) ^ 1, limit_ns, &abort_flag)) { ok = false; break; }
+      const unsigned char* usrc;
+      uint32_t ubytes = 0;
+      if (d.lev == 0) {
+        usrc = (const unsigned char*)(io.x + j * d.n0);
+        ubytes = inputs_bulk ? (uint32_t)(d.n0 * VS) : 0;
+      } else {
+        usrc = (const unsigned char*)(io.win + d.in_off[2 * j]);
+        ubytes = inputs_bulk ? (uint32_t)((d.in_len[2 * j] + d.in_len[2 * j + 1]) * VS) : 0;
+      }
+      const unsigned char* ua = (const unsigned char*)((uintptr_t)usrc & ~(uintptr_t)15);
+      const uint32_t ucopy = ubytes ? (uint32_t)((((uintptr_t)usrc + ubytes + 15) & ~(uintptr_t)15) - (uintptr_t)ua) : 0;
+      uint32_t icopy[2] = {0, 0};
+      const unsigned char* ia[2] = {nullptr, nullptr};
+      if (d.kind != KIND_S && inputs_bulk) {
+        for (int c = 0; c < 2; ++c) {
+          const unsigned char* is = (const unsigned char*)(d.idx + d.ioff[2 * j + c]);
+          const uint32_t ib = (uint32_t)((d.rows[2 * j + c] + d.cols[2 * j + c]) * 4);
+          ia[c] = (const unsigned char*)((uintptr_t)is & ~(uintptr_t)15);
+          icopy[c] = (uint32_t)((((uintptr_t)is + ib + 15) & ~(uintptr_t)15) - (uintptr_t)ia[c]);
+        }
+      }
+      if (producer_enabled) {
+        mbar_expect_tx(&in_full[b], ucopy + icopy[0] + icopy[1]);
+        if (ucopy) bulk_g2s(ubuf + (size_t)b * geo.ucap, ua, ucopy, &in_full[b]);
+        int32_t* ib0 = ibuf + (size_t)b * geo.icap;
+        if (icopy[0]) bulk_g2s(ib0, ia[0], icopy[0], &in_full[b]);
+        if (icopy[1]) bulk_g2s(ib0 + ((icopy[0] / 4 + 3) & ~3), ia[1], icopy[1], &in_full[b]);
+      }
+      // the blocks, a few whole columns per stage
       for (int c = 0; c < 2 && ok; ++c) {
         const int rows = d.rows[2 * j + c], cols = d.cols[2 * j + c];
         if (rows == 0 || cols == 0) continue;
-        const int cpc = cols_per_chunk(rows, ES);
+        const int cpc = cols_per_chunk(rows, ES, STAGE_BYTES);
         const unsigned char* base = (const unsigned char*)(mat + d.moff[2 * j + c]);
         for (int j0 = 0; j0 < cols; j0 += cpc, ++it) {
           const int nc = min(cpc, cols - j0);
@@ -638,11 +716,13 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)  // two CTAs (26 warps) per
       atomicOr(status, 1);
       abort_flag = 1;
       // let the copies already issued land before the CTA's shared memory goes away
-      for (uint32_t k = it > STAGES ? it - STAGES : 0; k < it; ++k) {
-        const uint64_t t0 = gtimer();
+      const uint64_t t0 = gtimer();
+      for (uint32_t k = it > STAGES ? it - STAGES : 0; k < it; ++k)
         while (!mbar_try_wait(&full[k % STAGES], (k / STAGES) & 1) && gtimer() - t0 < limit_ns) {
         }
-      }
+      for (uint32_t k = nn > 2 ? nn - 2 : 0; k <= nn; ++k)
+        while (!mbar_try_wait(&in_full[k & 1], (k >> 1) & 1) && gtimer() - t0 < limit_ns) {
+        }
     }
     return;
   }
@@ -651,46 +731,71 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)  // two CTAs (26 warps) per
   const int tc = threadIdx.x - 32;      // 0 .. NCT-1: prologue / epilogue index
   const int team = tc / TCT;
   const int tr = tc - team * TCT;       // row index within the team
-  uint32_t it = 0;
-  for (int64_t j = blockIdx.x; j < d.m; j += gridDim.x) {
-    consumer_sync();
+  uint32_t it = 0, nn = 0;
+  bool failed = false;
+  for (int64_t j = blockIdx.x; j < d.m; j += gridDim.x, ++nn) {
+    consumer_sync<NCT>();
     if (*(volatile int*)&cons_abort) break;
+    const int b = nn & 1;
     int l0, l1;
-    if (d.lev == 0) {
-      l0 = d.n0;
-      l1 = 0;
-      for (int i = tc; i < l0; i += NCT) u[i] = io.x[j * d.n0 + i];
-    } else {
-      l0 = d.in_len[2 * j];
-      l1 = d.in_len[2 * j + 1];
-      const int64_t o0 = d.in_off[2 * j];  // segments 2j and 2j+1 are adjacent
-      for (int i = tc; i < l0 + l1; i += NCT) u[i] = io.win[o0 + i];
-    }
+    if (d.lev == 0) { l0 = d.n0; l1 = 0; }
+    else { l0 = d.in_len[2 * j]; l1 = d.in_len[2 * j + 1]; }
     const int rows0 = d.rows[2 * j], rows1 = d.rows[2 * j + 1];
     const int cols0 = d.cols[2 * j], cols1 = d.cols[2 * j + 1];
-    const int32_t* ix0 = d.idx + d.ioff[2 * j];
-    const int32_t* ix1 = d.idx + d.ioff[2 * j + 1];
-    consumer_sync();
-    if (d.kind == KIND_V) {
-      for (int i = tc; i < cols0; i += NCT) g[i] = P::cvt(u[ix0[rows0 + i]]);
-      for (int i = tc; i < cols1; i += NCT) g[gcap + i] = P::cvt(u[ix1[rows1 + i]]);
-    } else if (d.kind == KIND_S) {
-      for (int i = tc; i < l0 + l1; i += NCT) g[i] = P::cvt(u[i]);
-    } else {
-      for (int i = tc; i < l0 + l1; i += NCT) g[i < l0 ? i : gcap + i - l0] = P::cvt(u[i]);
+    if (!failed && !wait_bounded(&in_full[b], (nn >> 1) & 1, limit_ns, &abort_flag)) failed = true;
+    // inputs (shifted within 16 bytes of the copy) and index lists in shared memory
+    const V* u;
+    {
+      const uintptr_t usrc = d.lev == 0 ? (uintptr_t)(io.x + j * d.n0) : (uintptr_t)(io.win + d.in_off[2 * j]);
+      u = ubuf + (size_t)b * geo.ucap + (int)((usrc & 15) / VS);
     }
-    consumer_sync();
-    bool failed = false;
+    if (!inputs_bulk) {  // plain loads by the consumers
+      V* uw = ubuf + (size_t)b * geo.ucap;
+      if (d.lev == 0) {
+        for (int i = tc; i < l0; i += NCT) uw[i] = io.x[j * d.n0 + i];
+      } else {
+        const V* src = io.win + d.in_off[2 * j];
+        for (int i = tc; i < l0 + l1; i += NCT) uw[i] = src[i];
+      }
+      u = uw;
+    }
+    const int32_t* ix0 = nullptr;
+    const int32_t* ix1 = nullptr;
+    if (d.kind != KIND_S) {
+      int32_t* ib0 = ibuf + (size_t)b * geo.icap;
+      if (inputs_bulk) {
+        const uintptr_t s0 = (uintptr_t)(d.idx + d.ioff[2 * j]), s1 = (uintptr_t)(d.idx + d.ioff[2 * j + 1]);
+        const uint32_t c0 = (uint32_t)((((s0 + (rows0 + cols0) * 4 + 15) & ~(uintptr_t)15)) - (s0 & ~(uintptr_t)15));
+        ix0 = ib0 + (int)((s0 & 15) / 4);
+        ix1 = ib0 + ((c0 / 4 + 3) & ~3) + (int)((s1 & 15) / 4);
+      } else {
+        const int32_t* g0 = d.idx + d.ioff[2 * j];
+        const int32_t* g1 = d.idx + d.ioff[2 * j + 1];
+        for (int i = tc; i < rows0 + cols0; i += NCT) ib0[i] = g0[i];
+        for (int i = tc; i < rows1 + cols1; i += NCT) ib0[rows0 + cols0 + i] = g1[i];
+        ix0 = ib0;
+        ix1 = ib0 + rows0 + cols0;
+      }
+    }
+    consumer_sync<NCT>();
+    // gathered operands: V: g = [u[p_0], u[p_1]]; S and U: g = u
+    if (!failed) {
+      if (d.kind == KIND_V) {
+        for (int i = tc; i < cols0; i += NCT) g[i] = P::cvt(u[ix0[rows0 + i]]);
+        for (int i = tc; i < cols1; i += NCT) g[cols0 + i] = P::cvt(u[ix1[rows1 + i]]);
+      } else {
+        for (int i = tc; i < l0 + l1; i += NCT) g[i] = P::cvt(u[i]);
+      }
+      if (d.kind == KIND_U)  // t[q_0] = in_0; t[p_0] comes from the block-0 products
+        for (int i = tc; i < l0; i += NCT) t[ix0[i]] = u[i];
+    }
+    consumer_sync<NCT>();
     const int tl = l0 + rows0;  // row-ID levels: |t| = |q_0| + |p_0|
-    if (d.kind == KIND_U) {
-      // t[q_0] = in_0 now; t[p_0] is written by the block-0 products below (q_0, p_0 partition t)
-      for (int i = tc; i < l0; i += NCT) t[ix0[i]] = u[i];
-    }
     for (int c = 0; c < 2; ++c) {
       const int rows = c ? rows1 : rows0, cols = c ? cols1 : cols0;
       const int32_t* ix = c ? ix1 : ix0;
-      const G* gc = g + (d.kind == KIND_S ? 0 : c * gcap);
-      if (d.kind == KIND_U && c == 1) {  // block 0 has written all of t (end-of-block sync)
+      const G* gc = g + (d.kind == KIND_S ? 0 : (d.kind == KIND_V ? c * cols0 : c * l0));
+      if (d.kind == KIND_U && c == 1 && !failed) {  // block 0 has written all of t
         for (int i = tc; i < l1; i += NCT) { V* q = &t[ix1[i]]; *q = P::add(*q, u[l0 + i]); }
       }
       typename P::acc_t acc[RPT];
@@ -698,23 +803,23 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)  // two CTAs (26 warps) per
       for (int k = 0; k < RPT; ++k) P::init(acc[k]);
       const bool work = rows > 0 && cols > 0;
       if (work) {
-        const int cpc = cols_per_chunk(rows, ES);
+        const int cpc = cols_per_chunk(rows, ES, STAGE_BYTES);
         const uintptr_t base = (uintptr_t)(mat + d.moff[2 * j + c]);
-        int ch = 0;
-        for (int j0 = 0; j0 < cols; j0 += cpc, ++it, ++ch) {
-          if ((ch & (TEAMS - 1)) != team) continue;  // the other team's chunk
+        const uint32_t chunk_bytes = (uint32_t)cpc * rows * ES;
+        int since = 0;
+        uintptr_t src = base;
+        for (int j0 = 0; j0 < cols; j0 += cpc, ++it, src += chunk_bytes) {
+          if ((int)(it % TEAMS) != team) continue;  // the other team's chunk (stage it % STAGES)
           const int nc = min(cpc, cols - j0);
           const int stg = it % STAGES;
           if (!failed && !wait_bounded(&full[stg], (it / STAGES) & 1, limit_ns, &abort_flag)) failed = true;
           if (!failed) {
-            const uintptr_t src = base + (uintptr_t)j0 * rows * ES;
-            const int shift = (int)((src & 15) / ES);
+            const int shift = ES == 16 ? 0 : (int)((src & 15) / ES);  // 16-byte entries are never shifted
             const M* st = (const M*)(stages + (size_t)stg * STAGE_BYTES) + shift + tr;
             if (RPT == 1) {
               if (tr < rows) {
 #pragma unroll 4
                 for (int jj = 0; jj < nc; ++jj) P::mac(acc[0], st[jj * rows], gc[j0 + jj]);
-                P::flush(acc[0]);
               }
             } else {
 #pragma unroll 2
@@ -724,36 +829,38 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)  // two CTAs (26 warps) per
                 for (int k = 0; k < RPT; ++k)
                   if (tr + k * TCT < rows) P::mac(acc[k], st[jj * rows + k * TCT], gv);
               }
+            }
+            since += nc;
+            if (since >= FLUSH_TERMS) {
 #pragma unroll
               for (int k = 0; k < RPT; ++k) P::flush(acc[k]);
+              since = 0;
             }
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[stg]);
         }
-        // team 1 hands its partial sums to team 0
-        if (team == 1) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) P::flush(acc[k]);
+        // teams 1.. hand their partial sums to team 0
+        if (team > 0) {
 #pragma unroll
           for (int k = 0; k < RPT; ++k)
-            if (tr + k * TCT < rows) red[k * TCT + tr] = P::part(acc[k]);
+            if (tr + k * TCT < rows) red[((team - 1) * RPT + k) * TCT + tr] = P::part(acc[k]);
         }
       }
-      consumer_sync();
-      if (work && team == 0) {
-#pragma unroll
-        for (int k = 0; k < RPT; ++k)
-          if (tr + k * TCT < rows) P::combine(acc[k], red[k * TCT + tr]);
-      }
-      // no early exit here: every consumer warp must reach the barrier at the end of the block
+      consumer_sync<NCT>();
+      // no early exit here: every consumer warp must reach the barriers of this block
       const int64_t s_out = d.lev < d.L ? out_seg_id(d, j, c) : 0;
-      if (team == 0 && !failed) {
+      if (work && team == 0 && !failed) {
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
           const int r = tr + k * TCT;
           if (r >= rows) continue;
+          for (int tm = 1; tm < TEAMS; ++tm) P::combine(acc[k], red[((tm - 1) * RPT + k) * TCT + tr]);
           const V v = P::fin(acc[k]);
           if (d.kind == KIND_U) {
-            V* q = &t[ix[l0 * (1 - c) + l1 * c + r]];
+            V* q = &t[ix[(c ? l1 : l0) + r]];
             *q = c ? P::add(*q, v) : v;
           } else {
             io.wout[d.out_off[s_out] + r] = d.kind == KIND_V ? P::add(v, u[ix[r]]) : v;
@@ -763,15 +870,17 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)  // two CTAs (26 warps) per
       if (d.kind == KIND_V && cols == 0 && !failed) {  // all skeleton: out = u[q]
         for (int r = tc; r < rows; r += NCT) io.wout[d.out_off[s_out] + r] = u[ix[r]];
       }
-      consumer_sync();  // red is reused by the next block; t must be complete before c = 1
+      consumer_sync<NCT>();  // red is reused by the next block; t must be complete before c = 1
     }
+    // the node's inputs and index lists are no longer read: release the buffer
+    if (tc == 0) mbar_arrive(&in_empty[b]);
     if (failed) {
       atomicOr(status, 1);
       abort_flag = 1;
       cons_abort = 1;
     }
     if (d.kind == KIND_U) {
-      consumer_sync();
+      consumer_sync<NCT>();
       if (*(volatile int*)&cons_abort) break;
       if (d.lev == d.L) {
         for (int i = tc; i < tl; i += NCT) io.y[j * d.n0 + i] = t[i];
@@ -783,6 +892,80 @@ __global__ void __launch_bounds__(strm::NTHREADS, 2)  // two CTAs (26 warps) per
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Forward level kernels for one right-hand side. Variant 0: the per-node kernel; variants
+// 1..6: the streaming kernel with ring layout A, B or C (see strm::Ring*), each with the node
+// inputs copied by the producer (odd variants) or loaded by the consumers (even variants).
+constexpr int kNumFwdVariants = 7;
+
+static int default_variant(int fmt) { return fmt == IDBF_STORE_C128 ? 0 : 1; }
+
+template <class P, class RG>
+static idbf_status launch_stream(Plan* p, int l, bool bulk, const void* x, IO<typename P::vec_t> io, cudaStream_t st) {
+  using V = typename P::vec_t;
+  const LevelInfo& li = p->lv[l];
+  if (!p->d_status || li.max_rows > strm::MAX_RPT * strm::TCT ||
+      li.max_rows * (int)sizeof(typename P::mat_t) > RG::STAGE_BYTES - 32)
+    return IDBF_EUNSUPPORTED;
+  const int rpt = li.max_rows <= strm::TCT ? 1 : 2;
+  const strm::Geo geo = strm::geometry<P, RG>(li.max_in, li.max_out, li.max_cols_pair, rpt);
+  // per-SM shared memory 228 KB: each CTA also reserves 1 KB and 128 B of static storage
+  if (geo.total > (size_t)(RG::CTAS == 1 ? 226 * 1024 : 112 * 1024)) return IDBF_EUNSUPPORTED;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned ctas = (unsigned)std::min<int64_t>(p->m, (int64_t)RG::CTAS * sms);
+  const int x_ok = ((uintptr_t)x % 16 == 0) && ((p->n0 * (int)sizeof(V)) % 16 == 0);
+  const int use_bulk = bulk && (l > 0 || x_ok);
+  const DevLevel d = p->level(l);
+  const typename P::mat_t* mat = (const typename P::mat_t*)p->lmat[fmt_of<P>()][l];
+  if (rpt == 1) {
+    IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_stream<P, RG, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
+    k_level_stream<P, RG, 1><<<ctas, RG::NTHREADS, geo.total, st>>>(d, mat, io, li.max_in, li.max_out, li.max_cols_pair,
+                                                                    use_bulk, p->d_status, p->wait_limit_ns,
+                                                                    p->producer_enabled);
+  } else {
+    IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_stream<P, RG, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
+    k_level_stream<P, RG, 2><<<ctas, RG::NTHREADS, geo.total, st>>>(d, mat, io, li.max_in, li.max_out, li.max_cols_pair,
+                                                                    use_bulk, p->d_status, p->wait_limit_ns,
+                                                                    p->producer_enabled);
+  }
+  IDBF_CUDA_TRY(cudaGetLastError());
+  return IDBF_OK;
+}
+
+template <class P>
+static idbf_status launch_fwd_variant(Plan* p, int l, int v, const void* x, void* y, const typename P::vec_t* win,
+                                      typename P::vec_t* wout, cudaStream_t st, int fmt) {
+  using V = typename P::vec_t;
+  IO<V> io;
+  io.x = (const V*)x; io.ldx = p->N; io.y = (V*)y; io.ldy = p->N; io.R = 1;
+  io.win = win; io.wout = wout;
+  if (v != 0 && fmt == IDBF_STORE_C128) return IDBF_EUNSUPPORTED;  // FP64: per-node kernel only
+  switch (v) {
+    case 1: return launch_stream<P, strm::RingA>(p, l, true, x, io, st);
+    case 2: return launch_stream<P, strm::RingA>(p, l, false, x, io, st);
+    case 3: return launch_stream<P, strm::RingB>(p, l, true, x, io, st);
+    case 4: return launch_stream<P, strm::RingB>(p, l, false, x, io, st);
+    case 5: return launch_stream<P, strm::RingC>(p, l, true, x, io, st);
+    case 6: return launch_stream<P, strm::RingC>(p, l, false, x, io, st);
+    default: break;
+  }
+  const LevelInfo& li = p->lv[l];
+  const DevLevel d = p->level(l);
+  const typename P::mat_t* mat = (const typename P::mat_t*)p->lmat[fmt][l];
+  const int gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
+  const int rcap = std::max(li.max_rows, li.max_cols);
+  const size_t sm = li.max_in * sizeof(V) + 2 * gcap * sizeof(typename P::gv_t) + 2 * rcap * sizeof(V) + li.max_out * sizeof(V);
+  if (sm > 200 * 1024) return IDBF_EUNSUPPORTED;
+  if (sm > 48 * 1024) IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_fwd<P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  int threads = ((li.max_rows_pair + 31) / 32) * 32;
+  threads = std::max(64, std::min(512, threads));
+  k_level_fwd<P, 1><<<dim3((unsigned)p->m, 1), threads, sm, st>>>(d, mat, io, gcap, rcap, li.max_in);
+  IDBF_CUDA_TRY(cudaGetLastError());
+  return IDBF_OK;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -827,28 +1010,13 @@ static idbf_status run_levels(Plan* p, const void* x, void* y, int64_t R, int64_
     const int gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
     const int rcap = std::max(li.max_rows, li.max_cols);
     dim3 grid((unsigned)p->m, (unsigned)((R + RB - 1) / RB));
-    // one right-hand side, forward, FP32-pair or FP32 arithmetic: the streaming kernel (FP64 FMA
-    // is bound by the FP64 pipe and runs faster in the per-node kernel, which keeps more warps)
-    if (!adjoint && RB == 1 && p->d_status && fmt != IDBF_STORE_C128 && li.max_rows <= strm::MAX_RPT * strm::TCT &&
-        li.max_rows * (int)sizeof(typename P::mat_t) <= strm::STAGE_BYTES - 32) {
-      const strm::Geo geo = strm::geometry<P>(li.max_in, li.max_out, gcap);
-      if (geo.total <= 112 * 1024) {
-        int dev = 0, sms = 152;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const unsigned ctas = (unsigned)std::min<int64_t>(p->m, 2 * (int64_t)sms);
-        if (li.max_rows <= strm::TCT) {
-          IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_stream<P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
-          k_level_stream<P, 1><<<ctas, strm::NTHREADS, geo.total, st>>>(d, mat, io, gcap, li.max_in, li.max_out,
-                                                                        p->d_status, p->wait_limit_ns, p->producer_enabled);
-        } else {
-          IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_stream<P, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
-          k_level_stream<P, 2><<<ctas, strm::NTHREADS, geo.total, st>>>(d, mat, io, gcap, li.max_in, li.max_out,
-                                                                        p->d_status, p->wait_limit_ns, p->producer_enabled);
-        }
-        IDBF_CUDA_TRY(cudaGetLastError());
-        continue;
-      }
+    if (!adjoint && RB == 1) {
+      // one right-hand side, forward: the per-level variant (autotuned, else the default)
+      const int v = p->tuned[fmt].size() > (size_t)l && p->tuned[fmt][l] >= 0 ? p->tuned[fmt][l] : default_variant(fmt);
+      idbf_status s = launch_fwd_variant<P>(p, l, v, x, y, io.win, io.wout, st, fmt);
+      if (s == IDBF_EUNSUPPORTED && v != 0) s = launch_fwd_variant<P>(p, l, 0, x, y, io.win, io.wout, st, fmt);
+      if (s != IDBF_OK) return s;
+      continue;
     }
     if (!adjoint) {
       const size_t sm = (size_t)RB * (li.max_in * sizeof(V) + 2 * gcap * sizeof(typename P::gv_t) +
@@ -957,6 +1125,53 @@ static idbf_status run_levels_scratch(Plan* p, const void* x, void* y, int64_t R
   return IDBF_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Autotuner: time every forward variant of every level (one right-hand side) and keep the fastest.
+template <class P>
+static idbf_status autotune_fmt(Plan* p, int fmt, cudaStream_t st, int reps, float* best_ms_out) {
+  using V = typename P::vec_t;
+  idbf_status s = ensure_workspace(p, 1);
+  if (s != IDBF_OK) return s;
+  void *x = nullptr, *y = nullptr;
+  IDBF_CUDA_TRY(cudaMalloc(&x, p->N * sizeof(V)));
+  if (cudaMalloc(&y, p->N * sizeof(V)) != cudaSuccess) { cudaFree(x); return IDBF_ENOMEM; }
+  cudaMemsetAsync(x, 0x3e, p->N * sizeof(V), st);
+  V* wb[2] = {(V*)p->d_ws, (V*)((char*)p->d_ws + (size_t)p->max_seg_total * 16)};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  p->tuned[fmt].assign(p->L + 1, -1);
+  s = run_levels<P, 1>(p, x, y, 1, p->N, false, st, fmt);  // fills the workspace with real values
+  float total = 0.f;
+  for (int l = 0; l <= p->L && s == IDBF_OK; ++l) {
+    const V* win = l > 0 ? wb[(l - 1) & 1] : nullptr;
+    V* wout = l < p->L ? wb[l & 1] : nullptr;
+    float best = 1e30f;
+    int bestv = default_variant(fmt);
+    for (int v = 0; v < kNumFwdVariants; ++v) {
+      idbf_status r = launch_fwd_variant<P>(p, l, v, x, y, win, wout, st, fmt);
+      if (r == IDBF_EUNSUPPORTED) continue;
+      if (r != IDBF_OK) { s = r; break; }
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < reps; ++k) launch_fwd_variant<P>(p, l, v, x, y, win, wout, st, fmt);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { s = IDBF_ECUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bestv = v; }
+    }
+    p->tuned[fmt][l] = bestv;
+    total += best / reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaFree(x);
+  cudaFree(y);
+  if (best_ms_out) *best_ms_out = total;
+  return s;
+}
+
 }  // namespace idbf
 
 extern "C" {
@@ -968,6 +1183,35 @@ idbf_status idbf_apply(idbf_plan h, const void* x, void* y, int64_t nrhs, int64_
 idbf_status idbf_apply_adjoint(idbf_plan h, const void* x, void* y, int64_t nrhs, int64_t ld, int32_t mode,
                                void* stream) {
   return idbf::apply_common(h, x, y, nrhs, ld, mode, stream, true);
+}
+
+idbf_status idbf_autotune(idbf_plan h, int32_t mode, int32_t reps, void* stream, float* apply_ms) {
+  using namespace idbf;
+  if (!h || reps < 1) return IDBF_EINVAL;
+  Plan* p = &h->p;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != p->device) return IDBF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (mode) {
+    case IDBF_MODE_FP64: return p->has_format(IDBF_STORE_C128) ? autotune_fmt<FP64P>(p, IDBF_STORE_C128, st, reps, apply_ms) : IDBF_EUNSUPPORTED;
+    case IDBF_MODE_DF64: return p->has_format(IDBF_STORE_DF64) ? autotune_fmt<DF64P>(p, IDBF_STORE_DF64, st, reps, apply_ms) : IDBF_EUNSUPPORTED;
+    case IDBF_MODE_FP32: return p->has_format(IDBF_STORE_C64) ? autotune_fmt<FP32P>(p, IDBF_STORE_C64, st, reps, apply_ms) : IDBF_EUNSUPPORTED;
+    default: return IDBF_EINVAL;
+  }
+}
+
+idbf_status idbf_set_level_variants(idbf_plan h, int32_t mode, const int32_t* variants, int32_t n) {
+  using namespace idbf;
+  if (!h || n < 0 || (n > 0 && !variants)) return IDBF_EINVAL;
+  Plan* p = &h->p;
+  if (n != 0 && n != p->L + 1) return IDBF_EINVAL;
+  const int fmt = mode == IDBF_MODE_FP64 ? IDBF_STORE_C128 : mode == IDBF_MODE_DF64 ? IDBF_STORE_DF64
+                : mode == IDBF_MODE_FP32 ? IDBF_STORE_C64 : -1;
+  if (fmt < 0) return IDBF_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (variants[i] < -1 || variants[i] >= kNumFwdVariants) return IDBF_EINVAL;
+  p->tuned[fmt].assign(variants, variants + n);
+  return IDBF_OK;
 }
 
 idbf_status idbf_apply_noalloc(idbf_plan h, const void* x, void* y, int64_t nrhs, int64_t ld, int32_t mode,

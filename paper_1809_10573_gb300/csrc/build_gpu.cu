@@ -756,7 +756,8 @@ idbf_status Builder::run_step(int side, int s) {
   for (int64_t id = 0; id < nid; ++id) klist[list_pos(side, s, id)] = out.k[id];
   for (int64_t i = 0; i < nid; ++i) out.list_off[i + 1] = out.list_off[i] + klist[i];
   cudaError_t e1 = cudaMalloc(&out.d_T, std::max<int64_t>(out.T_len, 1) * 16);
-  cudaError_t e2 = cudaMalloc((void**)&out.d_idx, std::max<int64_t>(out.idx_len, 1) * 4);
+  // +16 bytes: the apply copies index lists in 16-byte granules and may read up to 12 bytes past the end
+  cudaError_t e2 = cudaMalloc((void**)&out.d_idx, std::max<int64_t>(out.idx_len, 1) * 4 + 16);
   cudaError_t e3 = cudaMalloc((void**)&out.d_list, std::max<int64_t>(out.list_off[nid], 1) * 4);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
     cudaGetLastError();

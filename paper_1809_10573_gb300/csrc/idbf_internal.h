@@ -77,6 +77,7 @@ struct Plan {
   int* d_status = nullptr;              // device status word: bit 0 = a bounded wait timed out
   uint64_t wait_limit_ns = 2000000000ull;  // limit of every device-side wait (2 s)
   int producer_enabled = 1;             // 0 only in the timeout test (waits that nothing satisfies)
+  std::vector<int> tuned[3];            // per storage format: forward kernel variant per level (-1: default)
   size_t ws_bytes = 0;
   int rank_saturated = 0;
   double build_seconds = 0.0;

@@ -393,7 +393,7 @@ idbf_status idbf_import_factors(const idbf_host_factors* f, int32_t storage, voi
       if (e == cudaSuccess) e = cudaMemcpyAsync(p.lmat[IDBF_STORE_C128][l], colmajor.data(), tot * 16, cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess && itot > 0) {
-      e = cudaMalloc(&p.lidx[l], itot * sizeof(int32_t));
+      e = cudaMalloc(&p.lidx[l], itot * sizeof(int32_t) + 16);  // 16-byte granule reads may pass the end
       if (e == cudaSuccess) e = cudaMemcpyAsync(p.lidx[l], idx.data(), itot * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host staging buffers go out of scope
@@ -460,6 +460,9 @@ idbf_status idbf_stats(idbf_plan h, idbf_stats_t* s) {
   s->segment_entries = p.max_seg_total;
   s->build_seconds = p.build_seconds;
   s->device_bytes = (int64_t)p.device_bytes();
+  for (int f = 0; f < 3; ++f)
+    for (int l = 0; l < IDBF_MAX_LEVELS; ++l)
+      s->level_variant[f][l] = (l < (int)p.tuned[f].size()) ? p.tuned[f][l] : -1;
   return IDBF_OK;
 }
 

@@ -136,3 +136,25 @@ def test_bounded_waits_report_a_timeout_and_the_context_survives():
     y = plan.apply(xd, mode=P.MODE_DF64)
     plan.sync_status()
     assert rel(y.cpu().numpy(), idbf.apply(c["F"], X)) < 1e-12
+
+
+@pytest.mark.parametrize("case", ["fio_base_8192_oddL", "dft_jit_2048_oddL"])
+@pytest.mark.parametrize("mode,fmt,tol", [(P.MODE_DF64, P.STORE_DF64, 1e-12), (P.MODE_FP32, P.STORE_C64, 2e-5)])
+def test_every_forward_variant_matches_oracle(case, mode, fmt, tol):
+    # the autotuner may pick any variant on any level: each must give the oracle's result
+    c, plan = _plan(case)
+    plan.set_storage(fmt)
+    X = inputs.complex_gaussian(c["N"], 1, seed=41)
+    dt = torch.complex128 if mode == P.MODE_DF64 else torch.complex64
+    xd = torch.from_numpy(X).to(dt).cuda()
+    ref = idbf.apply(c["F"], X)
+    for v in range(7):
+        plan.set_level_variants(mode, [v] * (c["F"].L + 1))
+        y = plan.apply(xd, mode=mode)
+        plan.sync_status()
+        assert rel(y.cpu().numpy(), ref) < tol, f"variant {v}"
+    ms = plan.autotune(mode, reps=2)
+    assert ms > 0
+    chosen = plan.stats()["level_variant"][fmt]
+    assert all(0 <= v < 7 for v in chosen)
+    assert rel(plan.apply(xd, mode=mode).cpu().numpy(), ref) < tol
