@@ -1051,12 +1051,15 @@ static idbf_status apply_common(idbf_plan h, const void* x, void* y, int64_t nrh
     case IDBF_MODE_FP64: fmt = IDBF_STORE_C128; break;
     case IDBF_MODE_DF64: fmt = IDBF_STORE_DF64; break;
     case IDBF_MODE_FP32: fmt = IDBF_STORE_C64; break;
-    default: return mode == IDBF_MODE_TF32X3 ? IDBF_EUNSUPPORTED : IDBF_EINVAL;
+    case IDBF_MODE_TF32X3: fmt = IDBF_STORE_C64; break;
+    default: return IDBF_EINVAL;
   }
   if (!p->has_format(fmt)) return IDBF_EUNSUPPORTED;
+  if (mode == IDBF_MODE_TF32X3 && adjoint) return IDBF_EUNSUPPORTED;
   idbf_status s = ensure_workspace(p, nrhs);
   if (s != IDBF_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
+  if (mode == IDBF_MODE_TF32X3) return apply_tf32x3(p, x, y, nrhs, ld, st);
   const bool one = nrhs == 1;
   switch (mode) {
     case IDBF_MODE_FP64: return one ? run_levels<FP64P, 1>(p, x, y, nrhs, ld, adjoint, st, fmt)

@@ -110,6 +110,9 @@ idbf_status convert_storage(Plan* p, uint32_t mask, cudaStream_t st);
 // workspace (apply.cu)
 idbf_status ensure_workspace(Plan* p, int64_t nrhs);
 
+// 3xTF32 tensor-core forward apply of all levels (apply_tc.cu); workspace must be reserved
+idbf_status apply_tf32x3(Plan* p, const void* x, void* y, int64_t R, int64_t ld, cudaStream_t st);
+
 inline int64_t boundary_index(int b, int64_t m) { return (int64_t)b * 2 * m; }
 
 }  // namespace idbf
