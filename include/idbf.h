@@ -200,6 +200,11 @@ idbf_status idbf_autotune(idbf_plan plan, int32_t mode, int32_t reps, void* stre
  * earlier idbf_autotune. A variant that does not fit a level falls back to variant 0. */
 idbf_status idbf_set_level_variants(idbf_plan plan, int32_t mode, const int32_t* variants, int32_t n);
 
+/* idbf_set_tc_split - operand splitting of the 3xTF32 tensor-core mode: 0 = x_hi + x_lo with
+ * x_hi = tf32(x) and three products (default), 1 = x_lo also rounded to TF32, 2 = four products
+ * (adds x_lo y_lo). */
+idbf_status idbf_set_tc_split(idbf_plan plan, int32_t split_mode);
+
 /* idbf_reserve - allocate the apply workspace for up to nrhs right-hand sides now. */
 idbf_status idbf_reserve(idbf_plan plan, int64_t nrhs);
 

@@ -64,6 +64,7 @@ SIGNATURES = {
                                      C.c_void_p]),
     "idbf_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_float)]),
     "idbf_set_level_variants": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
+    "idbf_set_tc_split": (C.c_int, [C.c_void_p, C.c_int32]),
     "idbf_reserve": (C.c_int, [C.c_void_p, C.c_int64]),
     "idbf_sync_status": (C.c_int, [C.c_void_p, C.c_void_p]),
     "idbf_debug_set_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32]),

@@ -11,10 +11,15 @@
 //   D (128 x 2 rows):              D(n, 2r) = Re (M G)(r, n), D(n, 2r+1) = Im (M G)(r, n).
 // Split precision (3xTF32, Ootomo and Yokota, "Recovering single precision accuracy from Tensor
 // Cores while surpassing the FP32 theoretical peak performance", IJHPCA 2022): x = x_hi + x_lo with
-// x_hi = rna_tf32(x), x_lo = x - x_hi, and A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi, accumulated in
-// FP32 in TMEM. Operands are staged by the CTA's warps into shared memory in the K-major,
-// no-swizzle canonical layout (8-row x 16-byte core matrices), double-buffered over K, and one
-// thread issues the MMAs; tcgen05.commit on an mbarrier tracks their completion.
+// x_hi = rna_tf32(x), x_lo = x - x_hi, and A B ~ A_hi B_hi + (A_hi B_lo + A_lo B_hi). The main
+// product and the two correction products go to separate TMEM accumulators (the correction terms
+// are ~2^-11 of the main ones and lose their low bits when added into the main accumulator) and
+// are summed in FP32 in the epilogue. The output rows of a block are covered in passes of at most
+// 192 real rows so that both accumulators fit in TMEM. Operands are staged by the CTA's warps
+// into shared memory in the K-major, no-swizzle canonical layout (8-row x 16-byte core
+// matrices), three stages over K with the next chunk's global loads issued before the current
+// chunk is written; one thread issues the MMAs and tcgen05.commit on an mbarrier tracks their
+// completion.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,15 +32,20 @@ namespace tc {
 constexpr int NT = 256;          // threads per CTA (8 warps)
 constexpr int MR = 128;          // right-hand sides per tile (MMA M)
 constexpr int KC = 8;            // complex columns per staged chunk (16 real K)
-constexpr int NMAX = 384;        // max real output rows per block (N, two MMA tiles: 256 + 128)
+constexpr int NH = 192;          // real output rows per pass (MMA N <= 192; two passes cover 384)
+constexpr int MAXROWS = NH;      // complex rows per block supported (2 passes x 96)
 constexpr uint32_t SBO = 128;    // byte step between 8-row core-matrix groups
 constexpr uint32_t A_BYTES = MR * 2 * KC * 4;     // 8 KB
-constexpr uint32_t B_BYTES = NMAX * 2 * KC * 4;   // 24 KB
+constexpr uint32_t B_BYTES = NH * 2 * KC * 4;     // 12 KB
 constexpr uint32_t LBO_A = (MR / 8) * 128;        // byte step between 4-element K groups
-constexpr uint32_t LBO_B = (NMAX / 8) * 128;
-constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;  // hi and lo of both operands: 64 KB
-constexpr size_t SMEM = 2 * (size_t)STAGE + 64;        // two stages + barriers
+constexpr uint32_t LBO_B = (NH / 8) * 128;
+constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;  // hi and lo of both operands: 40 KB
+constexpr int NSTAGE = 3;
+constexpr size_t SMEM = NSTAGE * (size_t)STAGE + 64;   // stages + barriers
 constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t D_CORR = 256;                       // TMEM column of the correction accumulator
+constexpr int A_PER_T = MR * KC / NT;                  // 4 complex A values per thread per chunk
+constexpr int B_PER_T = (NH / 2) * KC / NT;            // 3 complex B values per thread per chunk
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint64_t gtimer() {
@@ -87,11 +97,14 @@ __device__ __forceinline__ float tf32_hi(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
-// two consecutive K elements (2k', 2k'+1) of one row: one 8-byte store per split
-__device__ __forceinline__ void put2(unsigned char* hi, unsigned char* lo, uint32_t off, float a, float b) {
+// two consecutive K elements (2k', 2k'+1) of one row: one 8-byte store per split; the lo part
+// is rounded to TF32 as well (rna) when round_lo is set, else left for the hardware to narrow
+__device__ __forceinline__ void put2(unsigned char* hi, unsigned char* lo, uint32_t off, float a, float b, int round_lo) {
   const float ah = tf32_hi(a), bh = tf32_hi(b);
   *(float2*)(hi + off) = make_float2(ah, bh);
-  *(float2*)(lo + off) = make_float2(a - ah, b - bh);
+  float al = a - ah, bl = b - bh;
+  if (round_lo) { al = tf32_hi(al); bl = tf32_hi(bl); }
+  *(float2*)(lo + off) = make_float2(al, bl);
 }
 
 // One launch per level; persistent CTAs over nodes. x / y: user blocks (column-major, ld);
@@ -99,10 +112,10 @@ __device__ __forceinline__ void put2(unsigned char* hi, unsigned char* lo, uint3
 __global__ void __launch_bounds__(NT, 1)
     k_level_tc(DevLevel d, const float2* __restrict__ mat, const float2* __restrict__ x, int64_t ldx,
                float2* __restrict__ y, int64_t ldy, const float2* __restrict__ win, float2* __restrict__ wout, int R,
-               int* __restrict__ status, uint64_t limit_ns) {
+               int* __restrict__ status, uint64_t limit_ns, int split_mode) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tmem_base;
-  uint64_t* bars = (uint64_t*)(sm + 2 * STAGE);  // [0,1]: stage s free (MMAs done), [2]: tile done
+  uint64_t* bars = (uint64_t*)(sm + NSTAGE * STAGE);  // [0, NSTAGE): stage free; [NSTAGE]: pass done
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&tmem_base)),
@@ -111,14 +124,15 @@ __global__ void __launch_bounds__(NT, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(&bars[i])), "r"(1) : "memory");
+    for (int i = 0; i <= NSTAGE; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(&bars[i])), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  uint32_t kcg = 0, tiles = 0;  // chunks and tiles issued by this CTA (mbarrier phases)
+  uint32_t kcg = 0, passes = 0;  // chunks and passes issued by this CTA (mbarrier phases)
   bool failed = false;
   const int nrt = (R + MR - 1) / MR;
 
@@ -127,7 +141,6 @@ __global__ void __launch_bounds__(NT, 1)
     int64_t ib0 = 0;
     if (d.lev == 0) { l0 = d.n0; l1 = 0; }
     else { l0 = d.in_len[2 * j]; l1 = d.in_len[2 * j + 1]; ib0 = d.in_off[2 * j]; }
-    const int rows0 = d.rows[2 * j];
     const int32_t* ix0 = d.idx + d.ioff[2 * j];
     const int32_t* ix1 = d.idx + d.ioff[2 * j + 1];
     // element e (of concat(in_0, in_1)), right-hand side n of the node input
@@ -179,107 +192,121 @@ __global__ void __launch_bounds__(NT, 1)
         }
         continue;
       }
-      const int nreal = 2 * rows;
-      const int n0t = nreal > 256 ? 256 : ((nreal + 15) & ~15);
-      const int n1t = nreal > 256 ? ((nreal - 256 + 15) & ~15) : 0;
       const int nkc = (cols + KC - 1) / KC;
+      const int npass = rows > NH / 2 ? 2 : 1;
       for (int rt = 0; rt < nrt && !failed; ++rt) {
         const int nr = min(MR, R - rt * MR);
-        for (int kc = 0; kc < nkc; ++kc, ++kcg) {
-          const int s = kcg & 1;
-          unsigned char* Ah = sm + (size_t)s * STAGE;
-          unsigned char* Al = Ah + A_BYTES;
-          unsigned char* Bh = Al + A_BYTES;
-          unsigned char* Bl = Bh + B_BYTES;
-          // the MMAs that last read stage s must be done
-          if (!wait_bounded(&bars[s], ((kcg >> 1) & 1) ^ 1, limit_ns)) { failed = true; break; }
-          // A: G^T chunk, 128 rhs x 2 KC real K
-          for (int i = tid; i < MR * KC; i += NT) {
-            const int kk = i / MR, n = i % MR, k = kc * KC + kk;
-            float2 gv = make_float2(0.f, 0.f);
-            if (k < cols && n < nr) gv = in_at(g_elem(k), rt * MR + n);
-            put2(Ah, Al, koff(n, 2 * kk, LBO_A), gv.x, gv.y);
+        for (int ps = 0; ps < npass && !failed; ++ps) {
+          const int r0 = ps * (NH / 2);                       // first complex row of the pass
+          const int prow = min(NH / 2, rows - r0);            // complex rows of the pass
+          const int nreal = (2 * prow + 15) & ~15;            // MMA N (multiple of 16)
+          // registers for one chunk's global operands (prefetched one chunk ahead)
+          float2 av[A_PER_T], bv[B_PER_T];
+          auto load = [&](int kc) {
+#pragma unroll
+            for (int t = 0; t < A_PER_T; ++t) {
+              const int i = tid + t * NT, kk = i / MR, n = i % MR, k = kc * KC + kk;
+              av[t] = (k < cols && n < nr) ? in_at(g_elem(k), rt * MR + n) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int t = 0; t < B_PER_T; ++t) {
+              const int i = tid + t * NT, kk = i / (NH / 2), r = i % (NH / 2), k = kc * KC + kk;
+              bv[t] = (k < cols && r < prow) ? M[(int64_t)k * rows + r0 + r] : make_float2(0.f, 0.f);
+            }
+          };
+          load(0);
+          for (int kc = 0; kc < nkc; ++kc, ++kcg) {
+            const int s = kcg % NSTAGE;
+            unsigned char* Ah = sm + (size_t)s * STAGE;
+            unsigned char* Al = Ah + A_BYTES;
+            unsigned char* Bh = Al + A_BYTES;
+            unsigned char* Bl = Bh + B_BYTES;
+            // the MMAs that last read stage s must be done
+            if (!wait_bounded(&bars[s], ((kcg / NSTAGE) & 1) ^ 1, limit_ns)) { failed = true; break; }
+#pragma unroll
+            for (int t = 0; t < A_PER_T; ++t) {
+              const int i = tid + t * NT, kk = i / MR, n = i % MR;
+              put2(Ah, Al, koff(n, 2 * kk, LBO_A), av[t].x, av[t].y, split_mode >= 1);
+            }
+#pragma unroll
+            for (int t = 0; t < B_PER_T; ++t) {
+              const int i = tid + t * NT, kk = i / (NH / 2), r = i % (NH / 2);
+              put2(Bh, Bl, koff(2 * r, 2 * kk, LBO_B), bv[t].x, -bv[t].y, split_mode >= 1);
+              put2(Bh, Bl, koff(2 * r + 1, 2 * kk, LBO_B), bv[t].y, bv[t].x, split_mode >= 1);
+            }
+            if (kc + 1 < nkc) load(kc + 1);  // in flight while this chunk's MMAs run
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              const uint32_t id = idesc_tf32((uint32_t)nreal, MR);
+              for (int ks = 0; ks < 2; ++ks) {  // K = 8 real per MMA: two 4-element core groups
+                const uint32_t ao = 2 * ks * LBO_A, bo = 2 * ks * LBO_B;
+                const uint64_t ah = sdesc(sa(Ah) + ao, LBO_A, SBO), al = sdesc(sa(Al) + ao, LBO_A, SBO);
+                const uint64_t bh = sdesc(sa(Bh) + bo, LBO_B, SBO), bl = sdesc(sa(Bl) + bo, LBO_B, SBO);
+                const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
+                mma_tf32(tmem, ah, bh, id, first);             // main: hi * hi
+                mma_tf32(tmem + D_CORR, ah, bl, id, first);    // corrections: hi * lo + lo * hi
+                mma_tf32(tmem + D_CORR, al, bh, id, 1u);
+                if (split_mode == 2) mma_tf32(tmem + D_CORR, al, bl, id, 1u);
+              }
+              commit(&bars[s]);
+              if (kc == nkc - 1) commit(&bars[NSTAGE]);
+            }
           }
-          // B: real embedding of M_c columns, 2 rows real rows x 2 KC real K (rows padded to NMAX)
-          for (int i = tid; i < (NMAX / 2) * KC; i += NT) {
-            const int kk = i / (NMAX / 2), r = i % (NMAX / 2), k = kc * KC + kk;
-            float2 mv = make_float2(0.f, 0.f);
-            if (k < cols && r < rows) mv = M[(int64_t)k * rows + r];
-            put2(Bh, Bl, koff(2 * r, 2 * kk, LBO_B), mv.x, -mv.y);
-            put2(Bh, Bl, koff(2 * r + 1, 2 * kk, LBO_B), mv.y, mv.x);
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncthreads();
-          if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t i0 = idesc_tf32(n0t, MR), i1 = n1t ? idesc_tf32(n1t, MR) : 0;
-            for (int ks = 0; ks < 2; ++ks) {  // K = 8 real per MMA: two 4-element core groups
-              const uint32_t ao = 2 * ks * LBO_A, bo = 2 * ks * LBO_B;
-              const uint64_t ah = sdesc(sa(Ah) + ao, LBO_A, SBO), al = sdesc(sa(Al) + ao, LBO_A, SBO);
-              const uint64_t bh0 = sdesc(sa(Bh) + bo, LBO_B, SBO), bl0 = sdesc(sa(Bl) + bo, LBO_B, SBO);
-              const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
-              mma_tf32(tmem, ah, bh0, i0, first);
-              mma_tf32(tmem, ah, bl0, i0, 1u);
-              mma_tf32(tmem, al, bh0, i0, 1u);
-              if (n1t) {  // output rows 128.. (real rows 256..): B starts 32 core groups later
-                const uint64_t bh1 = sdesc(sa(Bh) + bo + 32 * SBO, LBO_B, SBO), bl1 = sdesc(sa(Bl) + bo + 32 * SBO, LBO_B, SBO);
-                mma_tf32(tmem + 256, ah, bh1, i1, first);
-                mma_tf32(tmem + 256, ah, bl1, i1, 1u);
-                mma_tf32(tmem + 256, al, bh1, i1, 1u);
+          if (failed) break;
+          // epilogue: lane quadrant of warp w % 4 = 32 rhs; warps w and w + 4 split the columns
+          if (!wait_bounded(&bars[NSTAGE], passes & 1, limit_ns)) { failed = true; break; }
+          ++passes;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int q = warp & 3, half = warp >> 2;
+          const int n = rt * MR + q * 32 + lane;
+          for (int c0 = half * 16; c0 < nreal; c0 += 32) {
+            uint32_t v[16], w[16];
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]),
+                  "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]), "=r"(w[15])
+                : "r"(taddr + D_CORR));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (n >= R) continue;
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+              const int r = r0 + (c0 >> 1) + h;  // complex output row of the block
+              if ((c0 >> 1) + h >= prow) break;
+              const float2 res = make_float2(__uint_as_float(v[2 * h]) + __uint_as_float(w[2 * h]),
+                                             __uint_as_float(v[2 * h + 1]) + __uint_as_float(w[2 * h + 1]));
+              if (d.kind == KIND_V) {
+                const float2 uq = in_at(ix[r], n);
+                *out_ptr((c ? len_o0 : 0) + r, n) = make_float2(res.x + uq.x, res.y + uq.y);
+              } else if (d.kind == KIND_S) {
+                *out_ptr((c ? len_o0 : 0) + r, n) = res;
+              } else {
+                float2* p = out_ptr(ix[(c ? l1 : l0) + r], n);
+                if (c == 0) *p = res;
+                else { const float2 a = *p; *p = make_float2(a.x + res.x, a.y + res.y); }
               }
             }
-            commit(&bars[s]);
-            if (kc == nkc - 1) commit(&bars[2]);
           }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncthreads();  // TMEM read out before the next pass's MMAs overwrite it
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
-        if (failed) break;
-        // epilogue: lane quadrant of warp w % 4 = 32 rhs; warps w and w + 4 split the columns
-        if (!wait_bounded(&bars[2], tiles & 1, limit_ns)) { failed = true; break; }
-        ++tiles;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int q = warp & 3, half = warp >> 2;
-        const int n = rt * MR + q * 32 + lane;
-        const int ncol = n0t + n1t;
-        for (int c0 = half * 16; c0 < ncol; c0 += 32) {
-          uint32_t v[16];
-          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (n >= R) continue;
-#pragma unroll
-          for (int h = 0; h < 8; ++h) {
-            const int r = (c0 >> 1) + h;  // complex output row of the block
-            if (r >= rows) break;
-            const float2 res = make_float2(__uint_as_float(v[2 * h]), __uint_as_float(v[2 * h + 1]));
-            if (d.kind == KIND_V) {
-              const float2 uq = in_at(ix[r], n);
-              *out_ptr((c ? len_o0 : 0) + r, n) = make_float2(res.x + uq.x, res.y + uq.y);
-            } else if (d.kind == KIND_S) {
-              *out_ptr((c ? len_o0 : 0) + r, n) = res;
-            } else {
-              float2* p = out_ptr(ix[(c ? l1 : l0) + r], n);
-              if (c == 0) *p = res;
-              else { const float2 a = *p; *p = make_float2(a.x + res.x, a.y + res.y); }
-            }
-          }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // TMEM read out before the next tile's MMAs overwrite it
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       }
     }
     __syncthreads();
-    (void)rows0;
   }
   if (failed && (tid & 31) == 0) atomicOr(status, 1);
   // the last MMAs must have completed before the accumulators are released
   if (tid == 0 && kcg > 0) {
     const uint64_t t0 = gtimer();
-    while (!try_wait(&bars[(kcg - 1) & 1], ((kcg - 1) >> 1) & 1) && gtimer() - t0 < limit_ns) {
+    while (!try_wait(&bars[(kcg - 1) % NSTAGE], ((kcg - 1) / NSTAGE) & 1) && gtimer() - t0 < limit_ns) {
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -292,7 +319,7 @@ __global__ void __launch_bounds__(NT, 1)
 // the 3xTF32 apply of all levels (forward); returns EUNSUPPORTED if a block is too large
 idbf_status apply_tf32x3(Plan* p, const void* x, void* y, int64_t R, int64_t ld, cudaStream_t st) {
   for (int l = 0; l <= p->L; ++l)
-    if (p->lv[l].max_rows > tc::NMAX / 2) return IDBF_EUNSUPPORTED;
+    if (p->lv[l].max_rows > tc::MAXROWS) return IDBF_EUNSUPPORTED;
   IDBF_CUDA_TRY(cudaFuncSetAttribute(tc::k_level_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM));
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -306,7 +333,8 @@ idbf_status apply_tf32x3(Plan* p, const void* x, void* y, int64_t R, int64_t ld,
     float2* wout = l < p->L ? wb[l & 1] : nullptr;
     const unsigned ctas = (unsigned)std::min<int64_t>(p->m, sms);
     tc::k_level_tc<<<ctas, tc::NT, tc::SMEM, st>>>(d, (const float2*)p->lmat[IDBF_STORE_C64][l], (const float2*)x, ld,
-                                                  (float2*)y, ld, win, wout, (int)R, p->d_status, p->wait_limit_ns);
+                                                  (float2*)y, ld, win, wout, (int)R, p->d_status, p->wait_limit_ns,
+                                                  p->tc_split_mode);
     IDBF_CUDA_TRY(cudaGetLastError());
   }
   return IDBF_OK;

@@ -78,6 +78,7 @@ struct Plan {
   uint64_t wait_limit_ns = 2000000000ull;  // limit of every device-side wait (2 s)
   int producer_enabled = 1;             // 0 only in the timeout test (waits that nothing satisfies)
   std::vector<int> tuned[3];            // per storage format: forward kernel variant per level (-1: default)
+  int tc_split_mode = 0;                // tensor-core split: 0 three products, 1 lo rounded, 2 four products
   size_t ws_bytes = 0;
   int rank_saturated = 0;
   double build_seconds = 0.0;

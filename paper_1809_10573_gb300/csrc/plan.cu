@@ -431,6 +431,12 @@ idbf_status idbf_sync_status(idbf_plan h, void* stream) {
   return IDBF_OK;
 }
 
+idbf_status idbf_set_tc_split(idbf_plan h, int32_t split_mode) {
+  if (!h || split_mode < 0 || split_mode > 2) return IDBF_EINVAL;
+  h->p.tc_split_mode = split_mode;
+  return IDBF_OK;
+}
+
 idbf_status idbf_debug_set_wait(idbf_plan h, uint64_t limit_ns, int32_t producer_enabled) {
   if (!h || limit_ns == 0) return IDBF_EINVAL;
   h->p.wait_limit_ns = limit_ns;
