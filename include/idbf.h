@@ -224,6 +224,42 @@ idbf_status idbf_sync_status(idbf_plan plan, void* stream);
  * copies so that every consumer wait runs out. Not for production use. */
 idbf_status idbf_debug_set_wait(idbf_plan plan, uint64_t limit_ns, int32_t producer_enabled);
 
+/* ---- uneven batches: many operators in one persistent launch ---------------------------- */
+typedef struct idbf_batch_s* idbf_batch;
+
+/* idbf_batch_create - prepare the forward apply of nops plans (any N each), plan o with nrhs[o]
+ * right-hand sides, in `mode` (FP64, DF64 or FP32), as ONE persistent kernel launch captured in a
+ * CUDA graph. Work items (operator, level, run of nodes, block of right-hand sides) are queued in
+ * level order and taken by persistent CTAs; an item waits (bounded) until the previous level of
+ * its operator is complete. Allocates each operator's level workspace; the plans must outlive
+ * the batch and must not be changed (storage) while it exists. Synchronous. */
+idbf_status idbf_batch_create(const idbf_plan* plans, int32_t nops, const int64_t* nrhs, int32_t mode,
+                              idbf_batch* out);
+
+/* idbf_batch_apply - y[o] = K_o x[o] for every operator o (device pointers, column-major N_o x
+ * nrhs[o] blocks with leading dimension ld[o] >= N_o, element type of `mode`): one graph launch
+ * on `stream` after a small copy of the pointer table. */
+idbf_status idbf_batch_apply(idbf_batch b, const void* const* x, void* const* y, const int64_t* ld,
+                             void* stream);
+
+/* idbf_batch_autotune - time the batch for right-hand sides per item in {1, 4, 8} and nodes per
+ * item in {1, 2, 4} (reps launches each, on the given buffers) and keep the fastest; *best_ms
+ * receives its time per launch. Synchronous. */
+idbf_status idbf_batch_autotune(idbf_batch b, const void* const* x, void* const* y, const int64_t* ld,
+                                int32_t reps, void* stream, float* best_ms);
+
+/* idbf_batch_info - the current tiling: right-hand sides and nodes per work item, number of
+ * items, persistent CTAs. */
+idbf_status idbf_batch_info(idbf_batch b, int32_t* rhs_per_item, int32_t* nodes_per_item, int32_t* items,
+                            int32_t* ctas);
+
+/* idbf_batch_sync_status - wait for `stream`; IDBF_ETIMEOUT if a bounded wait of the batch kernel
+ * gave up since the last call (its results are invalid), IDBF_OK otherwise. */
+idbf_status idbf_batch_sync_status(idbf_batch b, void* stream);
+
+/* idbf_batch_destroy - release the batch (synchronises the device first; NULL is a no-op). */
+void idbf_batch_destroy(idbf_batch b);
+
 /* ---- statistics ------------------------------------------------------------------------- */
 #define IDBF_MAX_LEVELS 48
 typedef struct {

@@ -17,7 +17,7 @@ from ._lib import (KERNEL_DFT, KERNEL_FIO1D, MODE_DF64, MODE_FP32, MODE_FP64, MO
                    SAMPLE_ALL, SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, STORE_C64, STORE_C128,
                    STORE_DF64, IDBFError)
 
-__all__ = ["Plan", "IDBFError", "apply", "IDBFApply", "kernel_matvec_rows", "KERNEL_FIO1D", "KERNEL_DFT", "MODE_FP64",
+__all__ = ["Plan", "Batch", "IDBFError", "apply", "IDBFApply", "kernel_matvec_rows", "KERNEL_FIO1D", "KERNEL_DFT", "MODE_FP64",
            "MODE_DF64", "MODE_FP32", "MODE_TF32X3", "STORE_C128", "STORE_DF64", "STORE_C64",
            "SAMPLE_MOCK_CHEBYSHEV", "SAMPLE_RANDOM", "SAMPLE_ALL"]
 
@@ -177,6 +177,73 @@ class Plan:
     def close(self):
         if self._h is not None and self._h.value:
             _lib.lib().idbf_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Forward applies of several plans (uneven N, their own numbers of right-hand sides) in one
+    persistent kernel launch captured in a CUDA graph (idbf_batch_* in include/idbf.h)."""
+
+    def __init__(self, plans, nrhs, mode=MODE_DF64):
+        self.plans = list(plans)           # keep the plans alive as long as the batch
+        self.nrhs = [int(r) for r in nrhs]
+        self.mode = mode
+        n = len(self.plans)
+        hs = (C.c_void_p * n)(*[p._h.value for p in self.plans])
+        rs = (C.c_int64 * n)(*self.nrhs)
+        out = C.c_void_p()
+        _lib.check(_lib.lib().idbf_batch_create(hs, n, rs, mode, C.byref(out)), "idbf_batch_create")
+        self._h = out
+
+    def _tables(self, xs, ys):
+        n = len(self.plans)
+        dt = _VEC_DTYPE[self.mode]
+        xt = [_colmajor(x, p.N, dt) for x, p in zip(xs, self.plans)]
+        if ys is None:
+            yt = [torch.empty_like(t) for t in xt]
+        else:
+            yt = [y.t() if y.dim() == 2 else y[None, :] for y in ys]
+        for t, p, r in zip(yt, self.plans, self.nrhs):
+            if not (t.is_contiguous() and t.shape == (r, p.N) and t.dtype == dt):
+                raise ValueError("outputs must be column-major (N, nrhs) blocks of the mode's dtype")
+        xp = (C.c_void_p * n)(*[t.data_ptr() for t in xt])
+        yp = (C.c_void_p * n)(*[t.data_ptr() for t in yt])
+        ld = (C.c_int64 * n)(*[p.N for p in self.plans])
+        return xt, yt, xp, yp, ld
+
+    def apply(self, xs, ys=None, stream=None):
+        """ys[o] = K_o xs[o]; xs[o] of shape (N_o,) or (N_o, nrhs[o])."""
+        xt, yt, xp, yp, ld = self._tables(xs, ys)
+        _lib.check(_lib.lib().idbf_batch_apply(self._h, xp, yp, ld, _stream_ptr(stream)), "idbf_batch_apply")
+        self._keep = (xt, yt)
+        if ys is not None:
+            return ys
+        return [t[0] if x.dim() == 1 else t.t() for t, x in zip(yt, xs)]
+
+    def autotune(self, xs, reps=3, stream=None) -> float:
+        xt, yt, xp, yp, ld = self._tables(xs, None)
+        ms = C.c_float()
+        _lib.check(_lib.lib().idbf_batch_autotune(self._h, xp, yp, ld, reps, _stream_ptr(stream), C.byref(ms)),
+                   "idbf_batch_autotune")
+        return ms.value
+
+    def info(self) -> dict:
+        a, b, c, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _lib.check(_lib.lib().idbf_batch_info(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "idbf_batch_info")
+        return dict(rhs_per_item=a.value, nodes_per_item=b.value, items=c.value, ctas=d.value)
+
+    def sync_status(self, stream=None):
+        _lib.check(_lib.lib().idbf_batch_sync_status(self._h, _stream_ptr(stream)), "idbf_batch_sync_status")
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.lib().idbf_batch_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

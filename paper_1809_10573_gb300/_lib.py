@@ -70,6 +70,14 @@ SIGNATURES = {
     "idbf_debug_set_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32]),
     "idbf_set_storage": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p]),
     "idbf_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "idbf_batch_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
+    "idbf_batch_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "idbf_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                      C.POINTER(C.c_float)]),
+    "idbf_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int32)]),
+    "idbf_batch_sync_status": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "idbf_batch_destroy": (None, [C.c_void_p]),
     "idbf_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "idbf_load": (C.c_int, [C.c_char_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
     "idbf_destroy": (None, [C.c_void_p]),

@@ -1,0 +1,458 @@
+// An uneven batch of IDBF applies (operators of different N, each with its own number of
+// right-hand sides) in ONE persistent kernel launch, captured in a CUDA graph.
+//
+// Work items are (operator, level, run of nodes, block of right-hand sides). They are queued in
+// the order of the levels (all level-0 items of every operator, then all level-1 items, ...),
+// and persistent CTAs take them from the queue with an atomic counter. Before starting an item
+// of level l, a CTA waits until every item of level l-1 of the same operator has finished (a
+// per-(operator, level) completion counter). Those items are earlier in the queue, so they have
+// already been taken by CTAs that are running, and the wait ends: there is no cycle, whatever the
+// number of resident CTAs. Every wait is bounded in time; on a timeout the item is counted as done
+// (its results are invalid), bit 0 of the status word is set, and idbf_batch_sync_status reports
+// IDBF_ETIMEOUT.
+//
+// Each node is computed by fwd_node (level_kernels.cuh), the same body as the per-level kernel.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "idbf_internal.h"
+#include "level_kernels.cuh"
+
+namespace idbf {
+namespace bat {
+
+struct OpLevel {
+  DevLevel d;
+  const void* mat;
+  int gcap, rcap, max_in, pad;
+};
+struct OpDesc {
+  int L, R, level_base, pad;
+  void* ws0;
+  void* ws1;
+};
+struct Item {
+  int op, level, node0, nodes, r0, pad;
+};
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr int NT = 256;
+
+template <class P, int RB>
+__global__ void __launch_bounds__(NT) k_batch(const OpDesc* __restrict__ ops, const OpLevel* __restrict__ lv,
+                                              const Item* __restrict__ items, int nitems, const void* const* xs,
+                                              void* const* ys, const int64_t* lds, int* head, int* done,
+                                              const int* __restrict__ target, int* status, uint64_t limit_ns) {
+  using V = typename P::vec_t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int sidx, sfail;
+  for (;;) {
+    __syncthreads();  // the previous item's shared memory and sidx are no longer in use
+    if (threadIdx.x == 0) sidx = atomicAdd(head, 1);
+    __syncthreads();
+    const int i = sidx;
+    if (i >= nitems) break;
+    const Item w = items[i];
+    const OpDesc od = ops[w.op];
+    const int li = od.level_base + w.level;
+    if (threadIdx.x == 0) {
+      sfail = 0;
+      if (w.level > 0) {
+        volatile int* dp = done + (li - 1);
+        const int need = target[li - 1];
+        if (*dp < need) {
+          const uint64_t t0 = gtimer();
+          while (*dp < need) {
+            if (gtimer() - t0 > limit_ns) {
+              sfail = 1;
+              atomicOr(status, 1);
+              break;
+            }
+          }
+        }
+        __threadfence();  // acquire: the previous level's outputs are visible
+      }
+    }
+    __syncthreads();
+    if (!sfail) {
+      const OpLevel ol = lv[li];
+      IO<V> io;
+      io.x = (const V*)xs[w.op];
+      io.ldx = lds[w.op];
+      io.y = (V*)ys[w.op];
+      io.ldy = lds[w.op];
+      io.R = od.R;
+      V* wb[2] = {(V*)od.ws0, (V*)od.ws1};
+      io.win = w.level > 0 ? wb[(w.level - 1) & 1] : nullptr;
+      io.wout = w.level < od.L ? wb[w.level & 1] : nullptr;
+      for (int n = 0; n < w.nodes; ++n) {
+        if (n) __syncthreads();
+        fwd_node<P, RB>(ol.d, (const typename P::mat_t*)ol.mat, io, ol.gcap, ol.rcap, ol.max_in, (int64_t)(w.node0 + n),
+                        w.r0, smem);
+      }
+    }
+    __threadfence();  // release: this item's outputs before its completion count
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(done + li, 1);
+  }
+}
+
+template <class P, int RB>
+size_t node_smem(const LevelInfo& li) {
+  using V = typename P::vec_t;
+  const int gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
+  const int rcap = std::max(li.max_rows, li.max_cols);
+  return (size_t)RB * (li.max_in * sizeof(V) + 2 * gcap * sizeof(typename P::gv_t) + 2 * rcap * sizeof(V) +
+                       li.max_out * sizeof(V));
+}
+
+}  // namespace bat
+}  // namespace idbf
+
+using namespace idbf;
+
+struct idbf_batch_s {
+  int device = 0, nops = 0, mode = 0, fmt = 0;
+  std::vector<idbf_plan> plans;
+  std::vector<int64_t> R;
+  std::vector<void*> ws;
+  bat::OpDesc* d_ops = nullptr;
+  bat::OpLevel* d_lv = nullptr;
+  int nlevels_total = 0;
+  bat::Item* d_items = nullptr;
+  int nitems = 0;
+  int* d_counters = nullptr;  // head, then done[nlevels_total]
+  int* d_target = nullptr;
+  int* d_status = nullptr;
+  void** d_ptrs = nullptr;    // xs[nops], ys[nops], then lds[nops] (int64)
+  int rb = 4, npi = 1;
+  size_t smem = 0;
+  int ctas = 0;
+  uint64_t limit_ns = 2000000000ull;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+};
+
+namespace {
+
+void free_layout(idbf_batch_s* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_target) cudaFree(b->d_target);
+  if (b->d_counters) cudaFree(b->d_counters);
+  b->d_items = nullptr;
+  b->d_target = nullptr;
+  b->d_counters = nullptr;
+}
+
+template <class P, int RB>
+idbf_status launch_batch(idbf_batch_s* b, cudaStream_t st) {
+  if (b->smem > 48 * 1024)
+    IDBF_CUDA_TRY(cudaFuncSetAttribute(bat::k_batch<P, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+  const void* const* xs = (const void* const*)b->d_ptrs;
+  void* const* ys = (void* const*)(b->d_ptrs + b->nops);
+  const int64_t* lds = (const int64_t*)(b->d_ptrs + 2 * b->nops);
+  IDBF_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * (1 + b->nlevels_total), st));
+  bat::k_batch<P, RB><<<b->ctas, bat::NT, b->smem, st>>>(b->d_ops, b->d_lv, b->d_items, b->nitems, xs, ys, lds,
+                                                          b->d_counters, b->d_counters + 1, b->d_target, b->d_status,
+                                                          b->limit_ns);
+  IDBF_CUDA_TRY(cudaGetLastError());
+  return IDBF_OK;
+}
+
+template <class P>
+idbf_status launch_any(idbf_batch_s* b, cudaStream_t st) {
+  switch (b->rb) {
+    case 1: return launch_batch<P, 1>(b, st);
+    case 4: return launch_batch<P, 4>(b, st);
+    default: return launch_batch<P, 8>(b, st);
+  }
+}
+
+idbf_status launch(idbf_batch_s* b, cudaStream_t st) {
+  switch (b->mode) {
+    case IDBF_MODE_FP64: return launch_any<FP64P>(b, st);
+    case IDBF_MODE_DF64: return launch_any<DF64P>(b, st);
+    default: return launch_any<FP32P>(b, st);
+  }
+}
+
+template <class P, int RB>
+size_t smem_for(idbf_batch_s* b) {
+  size_t sm = 0;
+  for (int o = 0; o < b->nops; ++o)
+    for (const LevelInfo& li : b->plans[o]->p.lv) sm = std::max(sm, bat::node_smem<P, RB>(li));
+  return sm;
+}
+
+template <class P>
+size_t smem_any(idbf_batch_s* b) {
+  switch (b->rb) {
+    case 1: return smem_for<P, 1>(b);
+    case 4: return smem_for<P, 4>(b);
+    default: return smem_for<P, 8>(b);
+  }
+}
+
+template <class P, int RB>
+int occupancy(idbf_batch_s* b) {
+  int n = 0;
+  if (b->smem > 48 * 1024)
+    cudaFuncSetAttribute(bat::k_batch<P, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bat::k_batch<P, RB>, bat::NT, b->smem);
+  return std::max(n, 1);
+}
+
+template <class P>
+int occupancy_any(idbf_batch_s* b) {
+  switch (b->rb) {
+    case 1: return occupancy<P, 1>(b);
+    case 4: return occupancy<P, 4>(b);
+    default: return occupancy<P, 8>(b);
+  }
+}
+
+// Queue of items, completion targets and the captured graph for the current (rb, npi).
+idbf_status layout(idbf_batch_s* b) {
+  free_layout(b);
+  std::vector<bat::Item> items;
+  std::vector<int> target(b->nlevels_total, 0);
+  int maxL = 0, base = 0;
+  std::vector<int> lbase(b->nops);
+  for (int o = 0; o < b->nops; ++o) {
+    lbase[o] = base;
+    base += b->plans[o]->p.L + 1;
+    maxL = std::max(maxL, b->plans[o]->p.L);
+  }
+  for (int l = 0; l <= maxL; ++l)
+    for (int o = 0; o < b->nops; ++o) {
+      const Plan& p = b->plans[o]->p;
+      if (l > p.L) continue;
+      for (int r0 = 0; r0 < b->R[o]; r0 += b->rb)
+        for (int n0 = 0; n0 < p.m; n0 += b->npi) {
+          bat::Item it;
+          it.op = o;
+          it.level = l;
+          it.node0 = n0;
+          it.nodes = std::min(b->npi, p.m - n0);
+          it.r0 = r0;
+          it.pad = 0;
+          items.push_back(it);
+          ++target[lbase[o] + l];
+        }
+    }
+  b->nitems = (int)items.size();
+  switch (b->mode) {
+    case IDBF_MODE_FP64: b->smem = smem_any<FP64P>(b); break;
+    case IDBF_MODE_DF64: b->smem = smem_any<DF64P>(b); break;
+    default: b->smem = smem_any<FP32P>(b); break;
+  }
+  if (b->smem > 200 * 1024) return IDBF_EUNSUPPORTED;
+  int occ = 1;
+  switch (b->mode) {
+    case IDBF_MODE_FP64: occ = occupancy_any<FP64P>(b); break;
+    case IDBF_MODE_DF64: occ = occupancy_any<DF64P>(b); break;
+    default: occ = occupancy_any<FP32P>(b); break;
+  }
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  b->ctas = std::max(1, std::min(occ * sms, b->nitems));
+  IDBF_CUDA_TRY(cudaMalloc((void**)&b->d_items, sizeof(bat::Item) * std::max(1, b->nitems)));
+  IDBF_CUDA_TRY(cudaMalloc((void**)&b->d_target, sizeof(int) * b->nlevels_total));
+  IDBF_CUDA_TRY(cudaMalloc((void**)&b->d_counters, sizeof(int) * (1 + b->nlevels_total)));
+  IDBF_CUDA_TRY(cudaMemcpy(b->d_items, items.data(), sizeof(bat::Item) * b->nitems, cudaMemcpyHostToDevice));
+  IDBF_CUDA_TRY(cudaMemcpy(b->d_target, target.data(), sizeof(int) * b->nlevels_total, cudaMemcpyHostToDevice));
+  // capture: reset the counters, run the persistent kernel
+  IDBF_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  idbf_status s = launch(b, b->cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+  if (s != IDBF_OK) { if (g) cudaGraphDestroy(g); return s; }
+  if (e != cudaSuccess) { set_cuda_error(e); return IDBF_ECUDA; }
+  b->graph = g;
+  IDBF_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+  return IDBF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+idbf_status idbf_batch_create(const idbf_plan* plans, int32_t nops, const int64_t* nrhs, int32_t mode, idbf_batch* out) {
+  if (!out) return IDBF_EINVAL;
+  *out = nullptr;
+  if (!plans || !nrhs || nops < 1 || nops > (1 << 16)) return IDBF_EINVAL;
+  if (mode != IDBF_MODE_FP64 && mode != IDBF_MODE_DF64 && mode != IDBF_MODE_FP32) return IDBF_EINVAL;
+  const int fmt = mode == IDBF_MODE_FP64 ? IDBF_STORE_C128 : mode == IDBF_MODE_DF64 ? IDBF_STORE_DF64 : IDBF_STORE_C64;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int o = 0; o < nops; ++o) {
+    if (!plans[o] || nrhs[o] < 1 || nrhs[o] > (1 << 16) || plans[o]->p.device != dev) return IDBF_EINVAL;
+    if (!plans[o]->p.has_format(fmt)) return IDBF_EUNSUPPORTED;
+  }
+  idbf_batch_s* b = new (std::nothrow) idbf_batch_s();
+  if (!b) return IDBF_ENOMEM;
+  b->device = dev;
+  b->nops = nops;
+  b->mode = mode;
+  b->fmt = fmt;
+  b->plans.assign(plans, plans + nops);
+  b->R.assign(nrhs, nrhs + nops);
+  std::vector<bat::OpDesc> ods(nops);
+  std::vector<bat::OpLevel> lvs;
+  idbf_status s = IDBF_OK;
+  for (int o = 0; o < nops && s == IDBF_OK; ++o) {
+    const Plan& p = plans[o]->p;
+    const size_t half = (size_t)p.max_seg_total * nrhs[o] * 16;
+    void* w = nullptr;
+    cudaError_t e = cudaMalloc(&w, 2 * half);
+    if (e != cudaSuccess) { set_cuda_error(e); s = IDBF_ENOMEM; break; }
+    b->ws.push_back(w);
+    ods[o].L = p.L;
+    ods[o].R = (int)nrhs[o];
+    ods[o].level_base = (int)lvs.size();
+    ods[o].pad = 0;
+    ods[o].ws0 = w;
+    ods[o].ws1 = (char*)w + half;
+    for (int l = 0; l <= p.L; ++l) {
+      const LevelInfo& li = p.lv[l];
+      bat::OpLevel ol;
+      ol.d = p.level(l);
+      ol.mat = p.lmat[fmt][l];
+      ol.gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
+      ol.rcap = std::max(li.max_rows, li.max_cols);
+      ol.max_in = li.max_in;
+      ol.pad = 0;
+      lvs.push_back(ol);
+    }
+  }
+  b->nlevels_total = (int)lvs.size();
+  if (s == IDBF_OK) {
+    cudaError_t e = cudaMalloc((void**)&b->d_ops, sizeof(bat::OpDesc) * nops);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_lv, sizeof(bat::OpLevel) * lvs.size());
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_ptrs, sizeof(void*) * 3 * nops);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_ops, ods.data(), sizeof(bat::OpDesc) * nops, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_lv, lvs.data(), sizeof(bat::OpLevel) * lvs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { set_cuda_error(e); s = e == cudaErrorMemoryAllocation ? IDBF_ENOMEM : IDBF_ECUDA; }
+  }
+  if (s == IDBF_OK) s = layout(b);
+  if (s != IDBF_OK) {
+    idbf_batch_destroy(b);
+    return s;
+  }
+  *out = b;
+  return IDBF_OK;
+}
+
+idbf_status idbf_batch_apply(idbf_batch b, const void* const* x, void* const* y, const int64_t* ld, void* stream) {
+  if (!b || !x || !y || !ld) return IDBF_EINVAL;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != b->device) return IDBF_EINVAL;
+  std::vector<void*> tab(3 * b->nops);
+  for (int o = 0; o < b->nops; ++o) {
+    if (!x[o] || !y[o] || ld[o] < b->plans[o]->p.N) return IDBF_EINVAL;
+    tab[o] = (void*)x[o];
+    tab[b->nops + o] = y[o];
+    memcpy(&tab[2 * b->nops + o], &ld[o], sizeof(int64_t));
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // pageable source: the copy is staged before the call returns, so tab may go out of scope
+  IDBF_CUDA_TRY(cudaMemcpyAsync(b->d_ptrs, tab.data(), sizeof(void*) * tab.size(), cudaMemcpyHostToDevice, st));
+  IDBF_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+  return IDBF_OK;
+}
+
+idbf_status idbf_batch_autotune(idbf_batch b, const void* const* x, void* const* y, const int64_t* ld, int32_t reps,
+                                void* stream, float* best_ms) {
+  if (!b || reps < 1) return IDBF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int brb = b->rb, bnpi = b->npi;
+  const int rbs[3] = {1, 4, 8}, npis[3] = {1, 2, 4};
+  idbf_status s = IDBF_OK;
+  for (int a = 0; a < 3 && s == IDBF_OK; ++a)
+    for (int c = 0; c < 3 && s == IDBF_OK; ++c) {
+      b->rb = rbs[a];
+      b->npi = npis[c];
+      idbf_status r = layout(b);
+      if (r == IDBF_EUNSUPPORTED) continue;
+      if (r != IDBF_OK) { s = r; break; }
+      if ((s = idbf_batch_apply(b, x, y, ld, stream)) != IDBF_OK) break;  // warm-up
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < reps && s == IDBF_OK; ++k) s = idbf_batch_apply(b, x, y, ld, stream);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (ms < best) { best = ms; brb = b->rb; bnpi = b->npi; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->rb = brb;
+  b->npi = bnpi;
+  if (s == IDBF_OK) s = layout(b);
+  if (best_ms) *best_ms = best;
+  return s;
+}
+
+idbf_status idbf_batch_info(idbf_batch b, int32_t* rhs_per_item, int32_t* nodes_per_item, int32_t* items, int32_t* ctas) {
+  if (!b) return IDBF_EINVAL;
+  if (rhs_per_item) *rhs_per_item = b->rb;
+  if (nodes_per_item) *nodes_per_item = b->npi;
+  if (items) *items = b->nitems;
+  if (ctas) *ctas = b->ctas;
+  return IDBF_OK;
+}
+
+idbf_status idbf_batch_sync_status(idbf_batch b, void* stream) {
+  if (!b) return IDBF_EINVAL;
+  int v = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  IDBF_CUDA_TRY(cudaMemcpyAsync(&v, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IDBF_CUDA_TRY(cudaStreamSynchronize(st));
+  if (v) {
+    IDBF_CUDA_TRY(cudaMemset(b->d_status, 0, sizeof(int)));
+    return IDBF_ETIMEOUT;
+  }
+  return IDBF_OK;
+}
+
+void idbf_batch_destroy(idbf_batch b) {
+  if (!b) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != b->device) cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  free_layout(b);
+  for (void* w : b->ws) cudaFree(w);
+  if (b->d_ops) cudaFree(b->d_ops);
+  if (b->d_lv) cudaFree(b->d_lv);
+  if (b->d_ptrs) cudaFree(b->d_ptrs);
+  if (b->d_status) cudaFree(b->d_status);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (cur != b->device) cudaSetDevice(cur);
+  delete b;
+}
+
+}  // extern "C"
