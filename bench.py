@@ -371,6 +371,187 @@ def gpu_arm(args, rank, world, local):
     return 0
 
 
+# ---- further workloads (separate JSON lines; the default run is the single-vector apply) ------
+def gpu_mrhs(args, rank, world):
+    """Many right-hand sides: N = 2^18, eps = 1e-6, 256 RHS; complex FP32 factors with 3xTF32
+    tensor-core block products vs the FP64 apply of the same vectors on the same GPU."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1809_10573_gb300 as P
+    from paper_1809_10573_gb300 import inputs
+    N, R = 1 << 18, 256
+    x, xi = inputs.uniform_grid(N)
+    plan = P.Plan.build(x, xi, eps=EPS, leaf=LEAF, kernel="fio", c_profile=0, oversample=T_OVERSAMPLE,
+                        oversample_leaf=T_LEAF)
+    plan.set_storage(P.STORE_C128, P.STORE_C64)
+    X = torch.from_numpy(inputs.complex_gaussian(N, R, seed=3)).cuda()
+    X32 = X.to(torch.complex64)
+
+    def tm(mode, xx, steps):
+        for _ in range(args.warmup):
+            plan.apply(xx, mode=mode)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            y = plan.apply(xx, mode=mode)
+        e1.record()
+        torch.cuda.synchronize()
+        return y, e0.elapsed_time(e1) / 1e3 / steps
+
+    ytc, stc = tm(P.MODE_TF32X3, X32, args.steps)
+    plan.sync_status()
+    y64, s64 = tm(P.MODE_FP64, X, 1)
+    err = float(torch.linalg.norm(ytc.to(torch.complex128) - y64) / torch.linalg.norm(y64))
+    st = plan.stats()
+    flops = 24.0 * st["entries"] * R  # 8 real flops per complex entry and rhs, three split products
+    value, tmax = job_throughput(1.0, stc, world)
+    line = {"metric": "IDBF multi-RHS applies/s at N=2^18, 256 RHS (3xTF32 tensor cores, error vs FP64 stated)",
+            "value": value, "unit": "applies/s (256 rhs each)", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic",
+            "config": {"workload": "1D FIO N=2^18 eps=1e-6 leaf 64, 256 complex Gaussian RHS (seed 3), complex64 factors"},
+            "rel_err_vs_fp64": err, "vector_applies_per_s": value * R,
+            "roofline": {"bound": "tensor", "achieved": flops / stc / 1e12, "unit": "TFLOP/s",
+                         "peak": 1939.7 / 2, "peak_kind": "measured bf16 burst x 1/2 (nominal tf32:bf16 ratio)",
+                         "frac": flops / stc / 1e12 / (1939.7 / 2)},
+            "fp64_same_rhs": {"ms_per_apply": s64 * 1e3, "speedup_tf32x3_vs_fp64": s64 / stc}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def gpu_batch(args, rank, world):
+    """Uneven batch: 64 operators, N = 2^e with e uniform in [12, 18], the first half the FIO and
+    the second half the jittered DFT kernel, 1-32 RHS each, eps = 1e-6, one persistent launch in a
+    CUDA graph, tiles autotuned. Timed in FP32 (the line's value) and in double-float, each beside
+    the same 64 applies made one plan at a time; errors against the FP64 apply."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1809_10573_gb300 as P
+    from paper_1809_10573_gb300 import inputs
+    ops = inputs.uneven_batch(seed=4)
+    plans, xs = [], []
+    t0 = time.time()
+    for o in ops:
+        N = o["N"]
+        if o["kind"] == "fio":
+            x, xi = inputs.uniform_grid(N)
+            p = P.Plan.build(x, xi, eps=EPS, leaf=LEAF, kernel="fio", c_profile=0, oversample=T_OVERSAMPLE,
+                             oversample_leaf=T_LEAF)
+        else:
+            x, xi = inputs.jittered_grid(N, seed=o["seed"])
+            p = P.Plan.build(x, xi, eps=EPS, leaf=LEAF, kernel="dft", sign=-1)
+        plans.append(p)
+        xs.append(torch.from_numpy(inputs.complex_gaussian(N, o["nrhs"], seed=o["seed"])).cuda())
+    build_s = time.time() - t0
+    y64 = [p.apply(x, mode=P.MODE_FP64) for p, x in zip(plans, xs)]
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / steps
+
+    res = {}
+    # the factors of all 64 operators take ~190 GB per 16-byte format: convert in place, one
+    # format at a time (C128 -> double-float -> complex64)
+    for name, mode, store, vdt, eb in (("df64", P.MODE_DF64, P.STORE_DF64, torch.complex128, 16),
+                                       ("fp32", P.MODE_FP32, P.STORE_C64, torch.complex64, 8)):
+        for p in plans:
+            p.set_storage(store)
+        torch.cuda.synchronize()
+        xm = [x.to(vdt) for x in xs]
+        ym = [torch.empty_like(x) for x in xm]
+        b = P.Batch(plans, [o["nrhs"] for o in ops], mode=mode)
+        tuned_ms = b.autotune(xm, reps=2)
+        secs = timed(lambda: b.apply(xm, ym), args.steps)
+        b.sync_status()
+        err = max(float(torch.linalg.norm(y.to(torch.complex128) - r) / torch.linalg.norm(r)) for y, r in zip(ym, y64))
+        sep = timed(lambda: [p.apply(x, mode=mode) for p, x in zip(plans, xm)], max(1, args.steps // 4))
+        algo = sum(p.algorithmic_bytes(x.shape[1], eb, eb) for p, x in zip(plans, xs))
+        res[name] = {"ms_per_batch": secs * 1e3, "batches_per_s": 1.0 / secs, "algorithmic_GBps": algo / secs / 1e9,
+                     "algorithmic_bytes": algo, "max_rel_err_vs_fp64": err, "tiles": b.info(),
+                     "autotune_best_ms": tuned_ms, "separate_applies_ms": sep * 1e3,
+                     "speedup_vs_separate_applies": sep / secs}
+        b.close()
+    value, tmax = job_throughput(1.0, res["fp32"]["ms_per_batch"] / 1e3, world)
+    peak, kind = peaks()
+    r32 = res["fp32"]
+    line = {"metric": "IDBF uneven-batch applies/s (64 operators, N 2^12..2^18, 1-32 RHS, one persistent launch in a CUDA graph)",
+            "value": value, "unit": "batches/s (64 operator applies each)", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 ops, seed 4: FIO (ops 0-31) / jittered DFT (32-63), eps=1e-6, leaf 64, complex64 factors"},
+            "rel_err": {"max_over_ops_vs_fp64": r32["max_rel_err_vs_fp64"]},
+            "operator_applies_per_s": 64 * value, "vector_applies_per_s": sum(o["nrhs"] for o in ops) * value,
+            "roofline": {"bound": "hbm", "achieved": r32["algorithmic_GBps"], "peak": peak, "unit": "GB/s",
+                         "frac": r32["algorithmic_GBps"] / peak, "peak_kind": kind},
+            "modes": res, "build_seconds_total": build_s, "N": [o["N"] for o in ops], "nrhs": [o["nrhs"] for o in ops]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def gpu_autograd(args, rank, world):
+    """Differentiation: loss ||K x - b||^2 at N = 2^20, eps = 1e-6, complex FP32, 32 RHS; forward
+    apply and hand-written adjoint backward through torch.autograd."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1809_10573_gb300 as P
+    from paper_1809_10573_gb300 import inputs
+    N, R = 1 << 20, 32
+    x, xi = inputs.uniform_grid(N)
+    plan = P.Plan.build(x, xi, eps=EPS, leaf=LEAF, kernel="fio", c_profile=0, oversample=T_OVERSAMPLE,
+                        oversample_leaf=T_LEAF)
+    plan.set_storage(P.STORE_C64)
+    X = torch.from_numpy(inputs.complex_gaussian(N, R, seed=5)).to(torch.complex64).cuda()
+    B = torch.from_numpy(inputs.complex_gaussian(N, R, seed=6)).to(torch.complex64).cuda()
+
+    def step():
+        xv = X.clone().requires_grad_(True)
+        loss = ((P.apply(plan, xv, P.MODE_FP32) - B).abs() ** 2).sum()
+        loss.backward()
+        return loss, xv.grad
+
+    for _ in range(args.warmup):
+        step()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        loss, g = step()
+    e1.record()
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3 / args.steps
+    value, tmax = job_throughput(1.0, secs, world)
+    line = {"metric": "IDBF forward+backward steps/s at N=2^20, 32 RHS (loss ||Kx-b||^2, adjoint-butterfly backward)",
+            "value": value, "unit": "fwd+bwd/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tmax * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "1D FIO N=2^20 eps=1e-6 leaf 64, 32 RHS complex64 (x seed 5, b seed 6)"},
+            "loss": float(loss.detach()), "grad_norm": float(torch.linalg.norm(g))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,6 +561,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--log2n", type=int, default=20, help="N = 2^log2n (20 = the benchmarked workload)")
     ap.add_argument("--modes", default="df64,fp64,fp32", help="apply modes to time (df64 is the headline)")
+    ap.add_argument("--workload", choices=["apply", "mrhs", "batch", "autograd"], default="apply",
+                    help="apply: the headline single-vector apply at N=2^20; the others print their own lines")
     args = ap.parse_args()
     global N_LOG2
     N_LOG2 = args.log2n
@@ -389,6 +572,12 @@ def main():
     try:
         if args.impl == "reference":
             return cpu_arm(args, rank, world)
+        if args.workload == "mrhs":
+            return gpu_mrhs(args, rank, world)
+        if args.workload == "batch":
+            return gpu_batch(args, rank, world)
+        if args.workload == "autograd":
+            return gpu_autograd(args, rank, world)
         return gpu_arm(args, rank, world, local)
     finally:
         if world > 1:

@@ -10,17 +10,36 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "idbf_internal.h"
 #include "level_kernels.cuh"
 
 namespace idbf {
 
-template <class P, int RB>
+template <class P, int RB, int RPT = 0>
 __global__ void __launch_bounds__(512) k_level_fwd(DevLevel d, const typename P::mat_t* __restrict__ mat,
                                                    IO<typename P::vec_t> io, int gcap, int rcap, int max_in) {
   extern __shared__ __align__(16) unsigned char smem[];
-  fwd_node<P, RB>(d, mat, io, gcap, rcap, max_in, (int64_t)blockIdx.x, (int)blockIdx.y * RB, smem);
+  fwd_node<P, RB, RPT>(d, mat, io, gcap, rcap, max_in, (int64_t)blockIdx.x, (int)blockIdx.y * RB, smem);
+}
+
+// Several right-hand sides, FP32 / FP64 (fwd_node_tiled): node blockIdx.x, right-hand sides
+// blockIdx.y * RB ...
+template <class P>
+__host__ __device__ constexpr bool tiled_ok() {
+  return std::is_same<typename P::vec_t, typename P::gv_t>::value;
+}
+// The right-hand-side blocks of a node are adjacent CTAs (blockIdx.x = node * nblk + block), so
+// that their reads of the node's factors meet in L2.
+template <class P, int RB, int TC, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_level_fwd_tiled(DevLevel d, const typename P::mat_t* __restrict__ mat,
+                                                         IO<typename P::vec_t> io, int max_rows, int max_in,
+                                                         int max_out, int nblk) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if constexpr (tiled_ok<P>())
+    fwd_node_tiled<P, RB, TC>(d, mat, io, max_rows, max_in, max_out, (int64_t)(blockIdx.x / nblk),
+                              (int)(blockIdx.x % nblk) * RB, smem);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -687,14 +706,38 @@ static idbf_status run_levels(Plan* p, const void* x, void* y, int64_t R, int64_
       if (s != IDBF_OK) return s;
       continue;
     }
+    if constexpr (RB >= 8 && tiled_ok<P>()) {
+      if (!adjoint) {
+      // several right-hand sides, FP32 / FP64: register tiles over streamed factor columns
+      // short blocks: 128 threads per CTA, so that more nodes (each a chain of dependent memory
+      // accesses) are in flight per SM
+      // (FP32: up to 85 registers per thread there), else 256 threads (FP32: up to 128 registers;
+      // FP64: unbounded, its tiles need more)
+      constexpr bool f32 = sizeof(V) == 8;
+      const bool small = f32 && li.max_rows <= 64;
+      const int nt = small ? 128 : 256;
+      const size_t sm = tiled::smem_bytes<P, RB, 4>(li.max_in, li.max_out, li.max_rows, nt);
+      if (sm <= 200 * 1024) {
+        auto kern = !f32 ? k_level_fwd_tiled<P, RB, 4, 1> : small ? k_level_fwd_tiled<P, RB, 4, f32 ? 3 : 1>
+                                                                  : k_level_fwd_tiled<P, RB, 4, f32 ? 2 : 1>;
+        if (sm > 48 * 1024)
+          IDBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const int nblk = (int)((R + RB - 1) / RB);
+        kern<<<(unsigned)(p->m * nblk), nt, sm, st>>>(d, mat, io, li.max_rows, li.max_in, li.max_out, nblk);
+        IDBF_CUDA_TRY(cudaGetLastError());
+        continue;
+      }
+      }
+    }
     if (!adjoint) {
-      const size_t sm = (size_t)RB * (li.max_in * sizeof(V) + 2 * gcap * sizeof(typename P::gv_t) +
-                                      2 * rcap * sizeof(V) + li.max_out * sizeof(V));
+      // several right-hand sides: (row, pair of right-hand sides, column slice) per thread
+      constexpr int RPT = RB >= 2 ? 2 : 1;
+      constexpr int NT = 256;
+      const size_t sm = fwd_node_smem<P, RB, RPT>(li.max_in, gcap, rcap, NT);
       if (sm > 200 * 1024) return IDBF_EUNSUPPORTED;
-      if (sm > 48 * 1024) IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_fwd<P, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      int threads = ((li.max_rows_pair + 31) / 32) * 32;
-      threads = std::max(64, std::min(512, threads));
-      k_level_fwd<P, RB><<<grid, threads, sm, st>>>(d, mat, io, gcap, rcap, li.max_in);
+      if (sm > 48 * 1024)
+        IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_fwd<P, RB, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_level_fwd<P, RB, RPT><<<grid, NT, sm, st>>>(d, mat, io, gcap, rcap, li.max_in);
     } else {
       const size_t sm = (size_t)RB * (li.max_out * sizeof(V) + 2 * gcap * sizeof(typename P::gv_t) +
                                       2 * rcap * sizeof(V) + li.max_in * sizeof(V));
@@ -730,13 +773,23 @@ static idbf_status apply_common(idbf_plan h, const void* x, void* y, int64_t nrh
   cudaStream_t st = (cudaStream_t)stream;
   if (mode == IDBF_MODE_TF32X3) return apply_tf32x3(p, x, y, nrhs, ld, st);
   const bool one = nrhs == 1;
+  // forward with several right-hand sides in FP32 / FP64: 16 per tile from 16 on, else 8
+  const bool wide = !adjoint && nrhs >= 16, mid = !adjoint && nrhs > 1;
+  idbf_status s2 = IDBF_EUNSUPPORTED;
   switch (mode) {
-    case IDBF_MODE_FP64: return one ? run_levels<FP64P, 1>(p, x, y, nrhs, ld, adjoint, st, fmt)
-                                    : run_levels<FP64P, 4>(p, x, y, nrhs, ld, adjoint, st, fmt);
+    case IDBF_MODE_FP64:
+      if (one) return run_levels<FP64P, 1>(p, x, y, nrhs, ld, adjoint, st, fmt);
+      if (wide) s2 = run_levels<FP64P, 16>(p, x, y, nrhs, ld, adjoint, st, fmt);
+      else if (mid) s2 = run_levels<FP64P, 8>(p, x, y, nrhs, ld, adjoint, st, fmt);
+      // a level too large for the wide tiles' shared memory: all levels again with 4 per tile
+      return s2 != IDBF_EUNSUPPORTED ? s2 : run_levels<FP64P, 4>(p, x, y, nrhs, ld, adjoint, st, fmt);
     case IDBF_MODE_DF64: return one ? run_levels<DF64P, 1>(p, x, y, nrhs, ld, adjoint, st, fmt)
                                     : run_levels<DF64P, 4>(p, x, y, nrhs, ld, adjoint, st, fmt);
-    default: return one ? run_levels<FP32P, 1>(p, x, y, nrhs, ld, adjoint, st, fmt)
-                        : run_levels<FP32P, 4>(p, x, y, nrhs, ld, adjoint, st, fmt);
+    default:
+      if (one) return run_levels<FP32P, 1>(p, x, y, nrhs, ld, adjoint, st, fmt);
+      if (wide) s2 = run_levels<FP32P, 16>(p, x, y, nrhs, ld, adjoint, st, fmt);
+      else if (mid) s2 = run_levels<FP32P, 8>(p, x, y, nrhs, ld, adjoint, st, fmt);
+      return s2 != IDBF_EUNSUPPORTED ? s2 : run_levels<FP32P, 4>(p, x, y, nrhs, ld, adjoint, st, fmt);
   }
 }
 

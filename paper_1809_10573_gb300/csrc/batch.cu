@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "idbf_internal.h"
@@ -28,7 +29,7 @@ namespace bat {
 struct OpLevel {
   DevLevel d;
   const void* mat;
-  int gcap, rcap, max_in, pad;
+  int gcap, rcap, max_in, max_out, max_rows, pad;
 };
 struct OpDesc {
   int L, R, level_base, pad;
@@ -47,8 +48,29 @@ __device__ __forceinline__ uint64_t gtimer() {
 
 constexpr int NT = 256;
 
-template <class P, int RB>
-__global__ void __launch_bounds__(NT) k_batch(const OpDesc* __restrict__ ops, const OpLevel* __restrict__ lv,
+// Tiles: right-hand sides per work item (RB); then either right-hand sides per thread (RPT, the
+// per-node body fwd_node, all precisions) or TC > 0: the tiled body fwd_node_tiled with TR x TC
+// register tiles and streamed factor columns (FP32 and FP64).
+struct Tile {
+  int rb, rpt, tc;
+};
+constexpr Tile kTiles[] = {{1, 1, 0}, {4, 2, 0}, {8, 2, 0}, {8, 4, 0}, {8, 0, 4}, {16, 0, 4}, {32, 0, 8}};
+constexpr int kNumTiles = 7;
+template <class P>
+__host__ __device__ constexpr int max_rb() {
+  return std::is_same<P, FP32P>::value ? 32 : std::is_same<P, FP64P>::value ? 16 : 8;
+}
+template <class P>
+__host__ __device__ constexpr bool tiled_ok() {
+  return std::is_same<typename P::vec_t, typename P::gv_t>::value;
+}
+template <class P, int T>
+constexpr bool instantiated() {
+  return kTiles[T].rb <= max_rb<P>() && (kTiles[T].tc == 0 || tiled_ok<P>());
+}
+
+template <class P, int RB, int RPT, int TC>
+__global__ void __launch_bounds__(NT, TC == 8 ? 1 : 2) k_batch(const OpDesc* __restrict__ ops, const OpLevel* __restrict__ lv,
                                               const Item* __restrict__ items, int nitems, const void* const* xs,
                                               void* const* ys, const int64_t* lds, int* head, int* done,
                                               const int* __restrict__ target, int* status, uint64_t limit_ns) {
@@ -96,8 +118,12 @@ __global__ void __launch_bounds__(NT) k_batch(const OpDesc* __restrict__ ops, co
       io.wout = w.level < od.L ? wb[w.level & 1] : nullptr;
       for (int n = 0; n < w.nodes; ++n) {
         if (n) __syncthreads();
-        fwd_node<P, RB>(ol.d, (const typename P::mat_t*)ol.mat, io, ol.gcap, ol.rcap, ol.max_in, (int64_t)(w.node0 + n),
-                        w.r0, smem);
+        if constexpr (TC > 0)
+          fwd_node_tiled<P, RB, TC>(ol.d, (const typename P::mat_t*)ol.mat, io, ol.max_rows, ol.max_in, ol.max_out,
+                                    (int64_t)(w.node0 + n), w.r0, smem);
+        else
+          fwd_node<P, RB, RPT>(ol.d, (const typename P::mat_t*)ol.mat, io, ol.gcap, ol.rcap, ol.max_in,
+                               (int64_t)(w.node0 + n), w.r0, smem);
       }
     }
     __threadfence();  // release: this item's outputs before its completion count
@@ -106,13 +132,14 @@ __global__ void __launch_bounds__(NT) k_batch(const OpDesc* __restrict__ ops, co
   }
 }
 
-template <class P, int RB>
+template <class P, int RB, int RPT, int TC>
 size_t node_smem(const LevelInfo& li) {
-  using V = typename P::vec_t;
   const int gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
   const int rcap = std::max(li.max_rows, li.max_cols);
-  return (size_t)RB * (li.max_in * sizeof(V) + 2 * gcap * sizeof(typename P::gv_t) + 2 * rcap * sizeof(V) +
-                       li.max_out * sizeof(V));
+  if constexpr (TC > 0)
+    return tiled::smem_bytes<P, RB, TC>(li.max_in, li.max_out, li.max_rows, NT);
+  else
+    return fwd_node_smem<P, RB, RPT>(li.max_in, gcap, rcap, NT);
 }
 
 }  // namespace bat
@@ -134,7 +161,7 @@ struct idbf_batch_s {
   int* d_target = nullptr;
   int* d_status = nullptr;
   void** d_ptrs = nullptr;    // xs[nops], ys[nops], then lds[nops] (int64)
-  int rb = 4, npi = 1;
+  int tile = 1, rb = 4, npi = 1;  // tile: index into bat::kTiles
   size_t smem = 0;
   int ctas = 0;
   uint64_t limit_ns = 2000000000ull;
@@ -158,76 +185,100 @@ void free_layout(idbf_batch_s* b) {
   b->d_counters = nullptr;
 }
 
-template <class P, int RB>
+template <class P, int T>
 idbf_status launch_batch(idbf_batch_s* b, cudaStream_t st) {
-  if (b->smem > 48 * 1024)
-    IDBF_CUDA_TRY(cudaFuncSetAttribute(bat::k_batch<P, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-  const void* const* xs = (const void* const*)b->d_ptrs;
-  void* const* ys = (void* const*)(b->d_ptrs + b->nops);
-  const int64_t* lds = (const int64_t*)(b->d_ptrs + 2 * b->nops);
-  IDBF_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * (1 + b->nlevels_total), st));
-  bat::k_batch<P, RB><<<b->ctas, bat::NT, b->smem, st>>>(b->d_ops, b->d_lv, b->d_items, b->nitems, xs, ys, lds,
-                                                          b->d_counters, b->d_counters + 1, b->d_target, b->d_status,
-                                                          b->limit_ns);
-  IDBF_CUDA_TRY(cudaGetLastError());
-  return IDBF_OK;
-}
-
-template <class P>
-idbf_status launch_any(idbf_batch_s* b, cudaStream_t st) {
-  switch (b->rb) {
-    case 1: return launch_batch<P, 1>(b, st);
-    case 4: return launch_batch<P, 4>(b, st);
-    default: return launch_batch<P, 8>(b, st);
+  constexpr int RB = bat::kTiles[T].rb, RPT = bat::kTiles[T].rpt, TC = bat::kTiles[T].tc;
+  if constexpr (!bat::instantiated<P, T>()) {
+    return IDBF_EUNSUPPORTED;
+  } else {
+    if (b->smem > 48 * 1024)
+      IDBF_CUDA_TRY(cudaFuncSetAttribute(bat::k_batch<P, RB, RPT, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)b->smem));
+    const void* const* xs = (const void* const*)b->d_ptrs;
+    void* const* ys = (void* const*)(b->d_ptrs + b->nops);
+    const int64_t* lds = (const int64_t*)(b->d_ptrs + 2 * b->nops);
+    IDBF_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * (1 + b->nlevels_total), st));
+    bat::k_batch<P, RB, RPT, TC><<<b->ctas, bat::NT, b->smem, st>>>(b->d_ops, b->d_lv, b->d_items, b->nitems, xs, ys, lds,
+                                                                 b->d_counters, b->d_counters + 1, b->d_target,
+                                                                 b->d_status, b->limit_ns);
+    IDBF_CUDA_TRY(cudaGetLastError());
+    return IDBF_OK;
   }
 }
+
+// shared memory per CTA: the largest node of any level of any operator (0 if the tile is not
+// instantiated for this precision)
+template <class P, int T>
+size_t smem_for(idbf_batch_s* b) {
+  constexpr int RB = bat::kTiles[T].rb, RPT = bat::kTiles[T].rpt, TC = bat::kTiles[T].tc;
+  if constexpr (!bat::instantiated<P, T>()) {
+    return 0;
+  } else {
+    size_t sm = 0;
+    for (int o = 0; o < b->nops; ++o)
+      for (const LevelInfo& li : b->plans[o]->p.lv) sm = std::max(sm, bat::node_smem<P, RB, RPT, TC>(li));
+    return sm;
+  }
+}
+
+template <class P, int T>
+int occupancy(idbf_batch_s* b) {
+  constexpr int RB = bat::kTiles[T].rb, RPT = bat::kTiles[T].rpt, TC = bat::kTiles[T].tc;
+  if constexpr (!bat::instantiated<P, T>()) {
+    return 1;
+  } else {
+    int n = 0;
+    if (b->smem > 48 * 1024)
+      cudaFuncSetAttribute(bat::k_batch<P, RB, RPT, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bat::k_batch<P, RB, RPT, TC>, bat::NT, b->smem);
+    return std::max(n, 1);
+  }
+}
+
+// calls F<P, tile>::run(b, args...) for the batch's precision and current tile
+#define IDBF_BATCH_DISPATCH(FN, RET_ON_BAD, ...)                                               \
+  [&]() {                                                                                      \
+    switch (b->mode) {                                                                         \
+      case IDBF_MODE_FP64: switch (b->tile) {                                                  \
+          case 0: return FN<FP64P, 0>(__VA_ARGS__); case 1: return FN<FP64P, 1>(__VA_ARGS__);  \
+          case 2: return FN<FP64P, 2>(__VA_ARGS__); case 3: return FN<FP64P, 3>(__VA_ARGS__);  \
+          case 4: return FN<FP64P, 4>(__VA_ARGS__); case 5: return FN<FP64P, 5>(__VA_ARGS__);  \
+          case 6: return FN<FP64P, 6>(__VA_ARGS__);                                            \
+          default: return RET_ON_BAD; }                                                        \
+      case IDBF_MODE_DF64: switch (b->tile) {                                                  \
+          case 0: return FN<DF64P, 0>(__VA_ARGS__); case 1: return FN<DF64P, 1>(__VA_ARGS__);  \
+          case 2: return FN<DF64P, 2>(__VA_ARGS__); case 3: return FN<DF64P, 3>(__VA_ARGS__);  \
+          case 4: return FN<DF64P, 4>(__VA_ARGS__); case 5: return FN<DF64P, 5>(__VA_ARGS__);  \
+          case 6: return FN<DF64P, 6>(__VA_ARGS__);                                            \
+          default: return RET_ON_BAD; }                                                        \
+      default: switch (b->tile) {                                                              \
+          case 0: return FN<FP32P, 0>(__VA_ARGS__); case 1: return FN<FP32P, 1>(__VA_ARGS__);  \
+          case 2: return FN<FP32P, 2>(__VA_ARGS__); case 3: return FN<FP32P, 3>(__VA_ARGS__);  \
+          case 4: return FN<FP32P, 4>(__VA_ARGS__); case 5: return FN<FP32P, 5>(__VA_ARGS__);  \
+          case 6: return FN<FP32P, 6>(__VA_ARGS__);                                            \
+          default: return RET_ON_BAD; }                                                        \
+    }                                                                                          \
+  }()
 
 idbf_status launch(idbf_batch_s* b, cudaStream_t st) {
-  switch (b->mode) {
-    case IDBF_MODE_FP64: return launch_any<FP64P>(b, st);
-    case IDBF_MODE_DF64: return launch_any<DF64P>(b, st);
-    default: return launch_any<FP32P>(b, st);
-  }
+  return IDBF_BATCH_DISPATCH(launch_batch, IDBF_EINVAL, b, st);
 }
 
-template <class P, int RB>
-size_t smem_for(idbf_batch_s* b) {
-  size_t sm = 0;
-  for (int o = 0; o < b->nops; ++o)
-    for (const LevelInfo& li : b->plans[o]->p.lv) sm = std::max(sm, bat::node_smem<P, RB>(li));
-  return sm;
-}
-
-template <class P>
-size_t smem_any(idbf_batch_s* b) {
-  switch (b->rb) {
-    case 1: return smem_for<P, 1>(b);
-    case 4: return smem_for<P, 4>(b);
-    default: return smem_for<P, 8>(b);
-  }
-}
-
-template <class P, int RB>
-int occupancy(idbf_batch_s* b) {
-  int n = 0;
-  if (b->smem > 48 * 1024)
-    cudaFuncSetAttribute(bat::k_batch<P, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bat::k_batch<P, RB>, bat::NT, b->smem);
-  return std::max(n, 1);
-}
-
-template <class P>
-int occupancy_any(idbf_batch_s* b) {
-  switch (b->rb) {
-    case 1: return occupancy<P, 1>(b);
-    case 4: return occupancy<P, 4>(b);
-    default: return occupancy<P, 8>(b);
+bool tile_valid(int mode, int tile) {
+  if (tile < 0 || tile >= bat::kNumTiles) return false;
+  const bat::Tile t = bat::kTiles[tile];
+  switch (mode) {
+    case IDBF_MODE_FP64: return t.rb <= bat::max_rb<FP64P>();
+    case IDBF_MODE_DF64: return t.rb <= bat::max_rb<DF64P>() && t.tc == 0;
+    default: return t.rb <= bat::max_rb<FP32P>();
   }
 }
 
 // Queue of items, completion targets and the captured graph for the current (rb, npi).
 idbf_status layout(idbf_batch_s* b) {
   free_layout(b);
+  if (!tile_valid(b->mode, b->tile)) return IDBF_EUNSUPPORTED;
+  b->rb = bat::kTiles[b->tile].rb;
   std::vector<bat::Item> items;
   std::vector<int> target(b->nlevels_total, 0);
   int maxL = 0, base = 0;
@@ -241,8 +292,10 @@ idbf_status layout(idbf_batch_s* b) {
     for (int o = 0; o < b->nops; ++o) {
       const Plan& p = b->plans[o]->p;
       if (l > p.L) continue;
-      for (int r0 = 0; r0 < b->R[o]; r0 += b->rb)
-        for (int n0 = 0; n0 < p.m; n0 += b->npi) {
+      // the right-hand-side blocks of a run of nodes are neighbours in the queue, so the
+      // blocks' second and later reads of the factors come from L2
+      for (int n0 = 0; n0 < p.m; n0 += b->npi)
+        for (int r0 = 0; r0 < b->R[o]; r0 += b->rb) {
           bat::Item it;
           it.op = o;
           it.level = l;
@@ -255,18 +308,10 @@ idbf_status layout(idbf_batch_s* b) {
         }
     }
   b->nitems = (int)items.size();
-  switch (b->mode) {
-    case IDBF_MODE_FP64: b->smem = smem_any<FP64P>(b); break;
-    case IDBF_MODE_DF64: b->smem = smem_any<DF64P>(b); break;
-    default: b->smem = smem_any<FP32P>(b); break;
-  }
-  if (b->smem > 200 * 1024) return IDBF_EUNSUPPORTED;
-  int occ = 1;
-  switch (b->mode) {
-    case IDBF_MODE_FP64: occ = occupancy_any<FP64P>(b); break;
-    case IDBF_MODE_DF64: occ = occupancy_any<DF64P>(b); break;
-    default: occ = occupancy_any<FP32P>(b); break;
-  }
+  if (!tile_valid(b->mode, b->tile)) return IDBF_EUNSUPPORTED;
+  b->smem = IDBF_BATCH_DISPATCH(smem_for, (size_t)0, b);
+  if (b->smem == 0 || b->smem > 200 * 1024) return IDBF_EUNSUPPORTED;
+  const int occ = IDBF_BATCH_DISPATCH(occupancy, 1, b);
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   b->ctas = std::max(1, std::min(occ * sms, b->nitems));
@@ -335,6 +380,8 @@ idbf_status idbf_batch_create(const idbf_plan* plans, int32_t nops, const int64_
       ol.gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
       ol.rcap = std::max(li.max_rows, li.max_cols);
       ol.max_in = li.max_in;
+      ol.max_out = li.max_out;
+      ol.max_rows = li.max_rows;
       ol.pad = 0;
       lvs.push_back(ol);
     }
@@ -351,7 +398,17 @@ idbf_status idbf_batch_create(const idbf_plan* plans, int32_t nops, const int64_
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) { set_cuda_error(e); s = e == cudaErrorMemoryAllocation ? IDBF_ENOMEM : IDBF_ECUDA; }
   }
-  if (s == IDBF_OK) s = layout(b);
+  if (s == IDBF_OK) {
+    // default tile: the largest preferred one whose shared memory fits
+    static const int pref_df[] = {3, 2, 1, 0}, pref_other[] = {5, 4, 3, 1, 0};
+    const int* pref = mode == IDBF_MODE_DF64 ? pref_df : pref_other;
+    const int npref = mode == IDBF_MODE_DF64 ? 4 : 5;
+    for (int k = 0; k < npref; ++k) {
+      b->tile = pref[k];
+      s = layout(b);
+      if (s != IDBF_EUNSUPPORTED) break;
+    }
+  }
   if (s != IDBF_OK) {
     idbf_batch_destroy(b);
     return s;
@@ -387,12 +444,13 @@ idbf_status idbf_batch_autotune(idbf_batch b, const void* const* x, void* const*
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int brb = b->rb, bnpi = b->npi;
-  const int rbs[3] = {1, 4, 8}, npis[3] = {1, 2, 4};
+  int btile = b->tile, bnpi = b->npi;
+  const int npis[3] = {1, 2, 4};
   idbf_status s = IDBF_OK;
-  for (int a = 0; a < 3 && s == IDBF_OK; ++a)
+  for (int a = 0; a < bat::kNumTiles && s == IDBF_OK; ++a)
     for (int c = 0; c < 3 && s == IDBF_OK; ++c) {
-      b->rb = rbs[a];
+      if (!tile_valid(b->mode, a)) continue;
+      b->tile = a;
       b->npi = npis[c];
       idbf_status r = layout(b);
       if (r == IDBF_EUNSUPPORTED) continue;
@@ -405,14 +463,31 @@ idbf_status idbf_batch_autotune(idbf_batch b, const void* const* x, void* const*
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= reps;
-      if (ms < best) { best = ms; brb = b->rb; bnpi = b->npi; }
+      if (ms < best) { best = ms; btile = b->tile; bnpi = b->npi; }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->rb = brb;
+  b->tile = btile;
   b->npi = bnpi;
   if (s == IDBF_OK) s = layout(b);
   if (best_ms) *best_ms = best;
+  return s;
+}
+
+idbf_status idbf_batch_set_tiling(idbf_batch b, int32_t tile, int32_t nodes_per_item) {
+  if (!b || tile < 0 || tile >= bat::kNumTiles) return IDBF_EINVAL;
+  if (nodes_per_item != 1 && nodes_per_item != 2 && nodes_per_item != 4) return IDBF_EINVAL;
+  if (!tile_valid(b->mode, tile)) return IDBF_EUNSUPPORTED;
+  const int old_tile = b->tile, old_npi = b->npi;
+  b->tile = tile;
+  b->npi = nodes_per_item;
+  idbf_status s = layout(b);
+  if (s == IDBF_EUNSUPPORTED) {
+    b->tile = old_tile;
+    b->npi = old_npi;
+    const idbf_status r = layout(b);
+    return r == IDBF_OK ? s : r;
+  }
   return s;
 }
 

@@ -12,6 +12,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "idbf_internal.h"
 
 namespace idbf {
@@ -208,22 +210,113 @@ __device__ __forceinline__ int64_t out_seg_id(const DevLevel& d, int64_t j, int 
   return (j / d.H) * 2 * d.H + j % d.H + c * d.H;
 }
 
+// Phase 3 of fwd_node for RPT > 0 (see there). Threads take tasks (slice s, group q, row gr) with
+// the row fastest, so a warp's loads of one column of a block are consecutive.
+template <class P, int RB, int RPT>
+__device__ __forceinline__ void block_products_split(const DevLevel& d, const typename P::mat_t* __restrict__ mat,
+                                                     const typename P::gv_t* g, typename P::vec_t* res,
+                                                     typename P::part_t* pbuf, int gcap, int rcap, int rows0,
+                                                     int rows1, int cols0, int cols1, int64_t mo0, int64_t mo1,
+                                                     int nrb) {
+  using M = typename P::mat_t;
+  using G = typename P::gv_t;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nrows = rows0 + rows1;
+  const int ng = (nrb + RPT - 1) / RPT;
+  const int tasks = nrows * ng;
+  const int maxc = max(cols0, cols1);
+  int S = 1;
+  while (S < 8 && 2 * S * tasks <= nt && maxc >= 16 * S) S *= 2;
+  for (int w = tid; w < tasks * S; w += nt) {
+    const int s = w / tasks, rem = w - s * tasks;
+    const int q = rem / nrows, gr = rem - q * nrows;
+    const int c = gr >= rows0;
+    const int r = c ? gr - rows0 : gr;
+    const int rows = c ? rows1 : rows0;
+    const int cols = c ? cols1 : cols0;
+    const int cb = (cols * s) / S, ce = (cols * (s + 1)) / S;
+    const M* Mc = mat + (c ? mo1 : mo0) + r;
+    const G* gc = g + (d.kind == KIND_S ? 0 : c * gcap * RB) + q * RPT;
+    typename P::acc_t acc[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) P::init(acc[k]);
+    int jj = cb;
+    for (; jj + P::CHUNK <= ce; jj += P::CHUNK) {
+#pragma unroll 8
+      for (int e = 0; e < P::CHUNK; ++e) {
+        const M mv = P::ld(Mc + (int64_t)(jj + e) * rows);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) P::mac(acc[k], mv, gc[(jj + e) * RB + k]);
+      }
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) P::flush(acc[k]);
+    }
+    for (; jj < ce; ++jj) {
+      const M mv = P::ld(Mc + (int64_t)jj * rows);
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) P::mac(acc[k], mv, gc[jj * RB + k]);
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) P::flush(acc[k]);
+    if (S == 1) {
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) res[(c * rcap + r) * RB + q * RPT + k] = P::fin(acc[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) pbuf[(size_t)w * RPT + k] = P::part(acc[k]);
+    }
+  }
+  if (S > 1) {
+    __syncthreads();
+    for (int i = tid; i < nrows * nrb; i += nt) {
+      const int gr = i / nrb, rb = i - gr * nrb;
+      const int q = rb / RPT, k = rb - q * RPT;
+      const int rem = q * nrows + gr;
+      typename P::acc_t a;
+      P::init(a);
+      for (int s = 0; s < S; ++s) P::combine(a, pbuf[(size_t)(s * tasks + rem) * RPT + k]);
+      const int c = gr >= rows0;
+      const int r = c ? gr - rows0 : gr;
+      res[(c * rcap + r) * RB + rb] = P::fin(a);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // forward level kernel. Shared memory: u[max_in][RB] (inputs), g[2][gcap][RB] (gathered
-// operands), res[2][rcap][RB] (block products), t[max_out][RB] (row-ID accumulation).
+// operands), res[2][rcap][RB] (block products), and for RPT > 0 a partial-sum buffer of
+// blockDim.x * RPT part_t (fwd_node_smem gives the total). The row-ID accumulation t[|t|][RB]
+// of a U level reuses g once the block products are done: |t| = |q_0| + |p_0| <= max_in +
+// max_rows <= 2 gcap, and sizeof(vec_t) <= sizeof(gv_t).
 // One node j of a level, right-hand sides r0 .. r0+RB-1, by the whole CTA (used by the per-level
-// kernel below and by the persistent batch kernel).
-template <class P, int RB>
+// kernels and by the persistent batch kernel).
+//
+// The block products (phase 3) are mapped one of two ways:
+//   RPT == 0: one thread per output row, all RB right-hand sides in registers;
+//   RPT  > 0: one thread per (output row, group of RPT right-hand sides, column slice). When the
+//             node has fewer (row, group) tasks than half the CTA, the columns are cut into
+//             S = 2, 4 or 8 slices whose partial sums are combined through shared memory, so
+//             that small blocks and single vectors still occupy the CTA.
+template <class P, int RB, int RPT>
+__host__ __device__ constexpr size_t fwd_node_smem(int max_in, int gcap, int rcap, int nthreads) {
+  static_assert(sizeof(typename P::vec_t) <= sizeof(typename P::gv_t), "t reuses g");
+  return (size_t)RB * (max_in * sizeof(typename P::vec_t) + 2 * gcap * sizeof(typename P::gv_t) +
+                       2 * rcap * sizeof(typename P::vec_t)) +
+         (RPT > 0 ? (size_t)nthreads * RPT * sizeof(typename P::part_t) : 0);
+}
+
+template <class P, int RB, int RPT = 0>
 __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::mat_t* __restrict__ mat,
                                          const IO<typename P::vec_t>& io, int gcap, int rcap, int max_in, int64_t j,
                                          int r0, unsigned char* smem) {
+  static_assert(RPT == 0 || RB % RPT == 0, "RB must be a multiple of RPT");
   using V = typename P::vec_t;
   using G = typename P::gv_t;
   using M = typename P::mat_t;
   V* u = (V*)smem;
   G* g = (G*)(u + (size_t)max_in * RB);
   V* res = (V*)(g + (size_t)2 * gcap * RB);
-  V* t = res + (size_t)2 * rcap * RB;
+  V* t = (V*)g;  // phase 4 of a U level only, after the last read of g
   const int nrb = min(RB, io.R - r0);
   const int tid = threadIdx.x, nt = blockDim.x;
 
@@ -264,7 +357,11 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
   }
   __syncthreads();
 
-  // phase 3: block products, one thread per output row
+  // phase 3: block products
+  if constexpr (RPT > 0) {
+    block_products_split<P, RB, RPT>(d, mat, g, res, (typename P::part_t*)(res + (size_t)2 * rcap * RB), gcap, rcap,
+                                     rows0, rows1, cols0, cols1, mo0, mo1, nrb);
+  } else {
   for (int gr = tid; gr < rows0 + rows1; gr += nt) {
     const int c = gr >= rows0;
     const int r = c ? gr - rows0 : gr;
@@ -296,6 +393,7 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
       P::flush(acc[rb]);
       res[(c * rcap + r) * RB + rb] = P::fin(acc[rb]);
     }
+  }
   }
   __syncthreads();
 
@@ -347,5 +445,286 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
   }
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// Tiled forward node for several right-hand sides (FP32 and FP64 policies, whose operands need
+// no conversion). One CTA computes node j for right-hand sides r0 .. r0+nrb-1 (nrb <= RB):
+//   - the node's inputs u[max_in][RB] and index lists are staged in shared memory once;
+//   - the columns of both blocks, block 0 then block 1, flow as one sequence of chunks of KC
+//     whole columns (contiguous in a column-major block) through a ring of STAGES shared-memory
+//     stages filled with cp.async, so the copies of the next chunks, also across the change of
+//     block, overlap the arithmetic of the current one;
+//   - every thread accumulates a TR x TC tile (TR rows interleaved by the number of row tiles,
+//     so that a warp reads consecutive rows of a staged column; TC consecutive right-hand sides
+//     read as one vector from u); when a block has fewer tiles than half the CTA, the columns of
+//     each chunk are dealt to S = 2, 4 or 8 slices held by neighbouring lanes, whose partial sums
+//     meet through warp shuffles;
+//   - outputs leave from registers: V and S levels write out_c = M_c u_c (+ u[q_c]) directly;
+//     a U level writes block 0's contributions to its output segment first and block 1 adds its
+//     own after a barrier (every output position receives exactly one term from each block, so
+//     the order of the two additions does not change the sum).
+namespace tiled {
+constexpr int TR = 4, KC = 8, STAGES = 3;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// bytes of one stage: KC columns of the tallest block (max_rows rows), plus room for a start
+// moved down to a 16-byte boundary and an end rounded up to one
+template <class P>
+__host__ __device__ constexpr size_t stage_bytes(int max_rows) {
+  return (((size_t)max_rows * KC * sizeof(typename P::mat_t) + 32) + 15) & ~(size_t)15;
+}
+// shared memory: u | ring | index lists
+template <class P, int RB, int TC>
+__host__ __device__ constexpr size_t smem_bytes(int max_in, int max_out, int max_rows, int nthreads) {
+  return (((size_t)max_in * RB * sizeof(typename P::vec_t) + 15) & ~(size_t)15) + STAGES * stage_bytes<P>(max_rows) +
+         2 * (size_t)((max_in > max_out ? max_in : max_out) + 4) * sizeof(int32_t) + 0 * nthreads;
+}
+
+// TC consecutive operands u[0 .. TC-1] (16-byte aligned)
+template <class P, int TC>
+__device__ __forceinline__ void load_ops(const typename P::vec_t* p, typename P::gv_t (&b)[TC]) {
+  if constexpr (sizeof(typename P::vec_t) == 8) {
+    static_assert(TC % 2 == 0, "pairs of complex64");
+#pragma unroll
+    for (int c = 0; c < TC; c += 2) {
+      const float4 v = *reinterpret_cast<const float4*>(p + c);
+      b[c] = make_float2(v.x, v.y);
+      b[c + 1] = make_float2(v.z, v.w);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < TC; ++c) b[c] = p[c];
+  }
+}
+
+// work split of one block over the CTA
+struct Split {
+  int rows, cols, nch;  // chunks of the block (0 if the block is empty)
+  int nrt, tasks;       // row tiles, (row tile, rhs group) tasks
+  int S, rounds;        // column slices per task (neighbouring lanes), passes over the block
+};
+__device__ __forceinline__ Split split_of(int rows, int cols, int nrb, int TC, int nt) {
+  Split q;
+  q.rows = rows;
+  q.cols = cols;
+  q.nch = (rows > 0 && cols > 0) ? (cols + KC - 1) / KC : 0;
+  q.nrt = (rows + TR - 1) / TR;
+  q.tasks = q.nrt * ((nrb + TC - 1) / TC);
+  q.S = 1;
+  while (q.S < 8 && q.S < KC && 2 * q.S * q.tasks <= nt) q.S *= 2;
+  q.rounds = q.S > 1 ? 1 : (q.tasks + nt - 1) / nt;
+  return q;
+}
+}  // namespace tiled
+
+template <class P, int RB, int TC>
+__device__ __forceinline__ void fwd_node_tiled(const DevLevel& d, const typename P::mat_t* __restrict__ mat,
+                                               const IO<typename P::vec_t>& io, int max_rows, int max_in,
+                                               int max_out, int64_t j, int r0, unsigned char* smem) {
+  using namespace tiled;
+  using V = typename P::vec_t;
+  using G = typename P::gv_t;
+  using M = typename P::mat_t;
+  using A = typename P::acc_t;
+  static_assert(std::is_same<V, G>::value, "operands used as stored (FP32 and FP64 policies)");
+  static_assert(RB % TC == 0 && (RB * sizeof(V)) % 16 == 0, "16-byte aligned operand rows");
+  constexpr int ES = (int)sizeof(M);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nrb = min(RB, io.R - r0);
+  V* u = (V*)smem;
+  unsigned char* ring = smem + (((size_t)max_in * RB * sizeof(V) + 15) & ~(size_t)15);
+  const size_t sbytes = stage_bytes<P>(max_rows);
+  int32_t* ixs = (int32_t*)(ring + STAGES * sbytes);
+  const int icap = (max_in > max_out ? max_in : max_out) + 4;
+
+  // node description
+  int l0, l1;
+  int64_t o0 = 0, o1 = 0;
+  if (d.lev == 0) {
+    l0 = d.n0;
+    l1 = 0;
+  } else {
+    l0 = d.in_len[2 * j];
+    l1 = d.in_len[2 * j + 1];
+    o0 = d.in_off[2 * j];
+    o1 = d.in_off[2 * j + 1];
+  }
+  const int64_t mov[2] = {d.moff[2 * j], d.moff[2 * j + 1]};
+  const Split sp[2] = {split_of(d.rows[2 * j], d.cols[2 * j], nrb, TC, nt),
+                       split_of(d.rows[2 * j + 1], d.cols[2 * j + 1], nrb, TC, nt)};
+  const int tot0 = sp[0].nch * sp[0].rounds;                // chunks of block 0 over all its passes
+  const int tot = tot0 + sp[1].nch * sp[1].rounds;
+
+  // stream chunk g of the node's sequence into stage g % STAGES (all threads; one commit group).
+  // Chunks are issued in order, so the block and chunk within it are tracked incrementally.
+  int ic = 0, iq = 0, ir = 0;  // block, chunk and pass of the next chunk to issue
+  if (sp[0].nch == 0) ic = 1;
+  auto issue = [&](int g) {
+    const int c = ic, q = iq;
+    if (++iq == sp[c].nch) {
+      iq = 0;
+      if (++ir == sp[c].rounds) { ir = 0; ic = 1; }
+    }
+    const int rows = sp[c].rows;
+    const int k0 = q * KC, kc = min(KC, sp[c].cols - k0);
+    const unsigned char* src = (const unsigned char*)(mat + mov[c] + (int64_t)k0 * rows);
+    const unsigned char* al = (const unsigned char*)((uintptr_t)src & ~(uintptr_t)15);
+    const unsigned char* end = (const unsigned char*)(((uintptr_t)(src + (size_t)kc * rows * ES) + 15) & ~(uintptr_t)15);
+    unsigned char* dst = ring + (size_t)(g % STAGES) * sbytes;
+    const int pieces = (int)((end - al) >> 4);
+    for (int p = tid; p < pieces; p += nt) cp_async16(dst + 16 * p, al + 16 * p);
+  };
+  // the first chunks go out before the inputs are loaded
+#pragma unroll
+  for (int g = 0; g < STAGES - 1; ++g) {
+    if (g < tot) issue(g);
+    cp_async_commit();
+  }
+
+  // inputs -> u (level 0: consecutive threads read consecutive elements of one column of x),
+  // index lists -> ixs
+  if (d.lev == 0) {
+    for (int i = tid; i < l0 * RB; i += nt) {
+      const int rb = i / l0, e = i - rb * l0;
+      u[e * RB + rb] = rb < nrb ? io.x[j * d.n0 + e + (int64_t)(r0 + rb) * io.ldx] : P::zero();
+    }
+  } else {
+    for (int i = tid; i < (l0 + l1) * RB; i += nt) {
+      const int e = i / RB, rb = i % RB;
+      const int64_t off = e < l0 ? o0 + e : o1 + (e - l0);
+      u[i] = rb < nrb ? io.win[off * io.R + r0 + rb] : P::zero();
+    }
+  }
+  if (d.kind != KIND_S) {
+    for (int c = 0; c < 2; ++c) {
+      const int n = sp[c].rows + (d.kind == KIND_V ? sp[c].cols : (c ? l1 : l0));
+      const int32_t* ix = d.idx + d.ioff[2 * j + c];
+      for (int i = tid; i < n; i += nt) ixs[c * icap + i] = ix[i];
+    }
+  }
+  __syncthreads();
+
+  // U levels: where output position e of the node lives
+  int len0 = 0;
+  int64_t b0 = 0, b1 = 0;
+  if (d.kind == KIND_U && d.lev < d.L) {
+    const int64_t s0 = out_seg_id(d, j, 0), s1 = out_seg_id(d, j, 1);
+    len0 = d.out_len[s0];
+    b0 = d.out_off[s0];
+    b1 = d.out_off[s1];
+  }
+  auto u_out = [&](int e, int rb) -> V* {
+    if (d.lev == d.L) return io.y + j * d.n0 + e + (int64_t)(r0 + rb) * io.ldy;
+    const int64_t off = e < len0 ? b0 + e : b1 + (e - len0);
+    return io.wout + off * io.R + r0 + rb;
+  };
+
+  int g = 0;  // position in the node's chunk sequence
+  for (int c = 0; c < 2; ++c) {
+    const Split bc = sp[c];
+    const int rows = bc.rows;
+    const int32_t* ixc = ixs + c * icap;
+    const int lc = c ? l1 : l0;
+    const int opbase = (d.kind == KIND_U && c) ? l0 : 0;  // U: block c multiplies in_c; S: all of u
+    int64_t ob = 0;
+    if (d.kind != KIND_U) ob = d.out_off[out_seg_id(d, j, c)];
+    const int S = bc.S;
+    for (int rd = 0; rd < bc.rounds && bc.tasks > 0; ++rd) {
+      const int w = S > 1 ? tid / S : rd * nt + tid;
+      const int sl = S > 1 ? tid - w * S : 0;
+      const bool active = w < bc.tasks;
+      const int ct = active ? w / bc.nrt : 0;
+      const int rt = active ? w - ct * bc.nrt : 0;
+      A acc[TR][TC];
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int cc = 0; cc < TC; ++cc) P::init(acc[i][cc]);
+      int roff[TR];
+#pragma unroll
+      for (int i = 0; i < TR; ++i) roff[i] = max(0, min(rt + i * bc.nrt, rows - 1));
+      for (int q = 0; q < bc.nch; ++q, ++g) {
+        cp_async_wait<STAGES - 2>();
+        __syncthreads();  // chunk g landed for every thread; the stage of chunk g-1 is free again
+        if (g + STAGES - 1 < tot) issue(g + STAGES - 1);
+        cp_async_commit();
+        if (active) {
+          const int k0 = q * KC, kc = min(KC, bc.cols - k0);
+          const unsigned char* stg = ring + (size_t)(g % STAGES) * sbytes;
+          const M* mc = (const M*)(stg + ((uintptr_t)(mat + mov[c] + (int64_t)k0 * rows) & 15));
+          auto column = [&](int kk) {
+            const int k = k0 + kk;
+            const int er = d.kind == KIND_V ? ixc[rows + k] : opbase + k;
+            G b[TC];
+            load_ops<P, TC>(u + (size_t)er * RB + ct * TC, b);
+            const M* mcol = mc + kk * rows;
+#pragma unroll
+            for (int i = 0; i < TR; ++i) {
+              const M mv = mcol[roff[i]];
+#pragma unroll
+              for (int cc = 0; cc < TC; ++cc) P::mac(acc[i][cc], mv, b[cc]);
+            }
+          };
+          if (S == 1 && kc == KC) {
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) column(kk);
+          } else {
+            for (int kk = sl; kk < kc; kk += S) column(kk);
+          }
+        }
+      }
+      // the S slices of a task are neighbouring lanes: combine their partial sums
+      for (int o = 1; o < S; o <<= 1) {
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+          for (int cc = 0; cc < TC; ++cc) {
+            acc[i][cc].re += __shfl_xor_sync(0xffffffffu, acc[i][cc].re, o);
+            acc[i][cc].im += __shfl_xor_sync(0xffffffffu, acc[i][cc].im, o);
+          }
+      }
+      if (active && sl == 0) {
+#pragma unroll
+        for (int i = 0; i < TR; ++i) {
+          const int r = rt + i * bc.nrt;
+          if (r >= rows) continue;
+#pragma unroll
+          for (int cc = 0; cc < TC; ++cc) {
+            const int rb = ct * TC + cc;
+            if (rb >= nrb) continue;
+            V v = P::fin(acc[i][cc]);
+            if (d.kind == KIND_U) {
+              V* dst = u_out(ixc[lc + r], rb);
+              *dst = c ? P::add(*dst, v) : v;
+            } else {
+              if (d.kind == KIND_V) v = P::add(v, u[(size_t)ixc[r] * RB + rb]);
+              io.wout[(ob + r) * io.R + r0 + rb] = v;
+            }
+          }
+        }
+      }
+    }
+    if (d.kind == KIND_U) {
+      // the inputs pass through to positions q_c
+      for (int i = tid; i < lc * nrb; i += nt) {
+        const int e = i / nrb, rb = i - e * nrb;
+        V* dst = u_out(ixc[e], rb);
+        const V v = u[(size_t)(opbase + e) * RB + rb];
+        *dst = c ? P::add(*dst, v) : v;
+      }
+      if (c == 0) __syncthreads();  // block 0's terms are in place before block 1 adds to them
+    }
+  }
+  cp_async_wait<0>();
+}
 
 }  // namespace idbf

@@ -5,6 +5,7 @@ import pytest
 import torch
 
 import paper_1809_10573_gb300 as P
+from paper_1809_10573_gb300 import _lib
 from oracle import idbf
 from paper_1809_10573_gb300 import inputs
 from tests.cases import oracle_case
@@ -42,10 +43,23 @@ def test_batch_matches_oracle_and_single_applies(mode, fmt, dt, tol):
         for y, ref, p, x in zip(ys, refs, plans, xs):
             assert rel(y.cpu().numpy(), ref) < tol
             assert rel(y.cpu().numpy(), p.apply(x, mode=mode).cpu().numpy()) < (1e-13 if tol < 1e-9 else 1e-6)
+    # every tiling the precision offers, then the autotuner's choice
+    for tile in range(len(P.Batch.TILES)):
+        try:
+            b.set_tiling(tile, nodes_per_item=2 if tile % 2 else 1)
+        except P.IDBFError as e:
+            rb, _, tc = P.Batch.TILES[tile]
+            max_rb = 32 if mode == P.MODE_FP32 else 16 if mode == P.MODE_FP64 else 8
+            assert e.status == _lib.EUNSUPPORTED and ((tc > 0 and mode == P.MODE_DF64) or rb > max_rb)
+            continue
+        ys = b.apply(xs)
+        b.sync_status()
+        for y, ref in zip(ys, refs):
+            assert rel(y.cpu().numpy(), ref) < tol, (tile, b.info())
     ms = b.autotune(xs, reps=2)
     assert ms > 0
     info = b.info()
-    assert info["rhs_per_item"] in (1, 4, 8) and info["nodes_per_item"] in (1, 2, 4) and info["items"] > 0
+    assert info["rhs_per_item"] in (1, 4, 8, 16, 32) and info["nodes_per_item"] in (1, 2, 4) and info["items"] > 0
     ys = b.apply(xs)
     b.sync_status()
     for y, ref in zip(ys, refs):
