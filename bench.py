@@ -324,7 +324,8 @@ def gpu_arm(args, rank, world, local):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind,
                 "traffic": (ratio * ab / (L + 1)) if ratio is not None else None,
-                "kernel": "k_level_fwd<DF64P,1> (every launch of the timed region)",
+                "kernel": "double-float level kernels (per level the autotuned k_level_stream ring or "
+                          "k_level_fwd; every launch of the timed region is one of them)",
                 "algorithmic_bytes_per_launch": ab / (L + 1)}
     # end to end through the C call: pinned host x -> device, apply, device -> host y
     xh = torch.from_numpy(g.copy()).pin_memory()
@@ -382,7 +383,7 @@ def gpu_mrhs(args, rank, world):
     __graft_entry__.build()
     import paper_1809_10573_gb300 as P
     from paper_1809_10573_gb300 import inputs
-    N, R = 1 << 18, 256
+    N, R = 1 << (args.log2n if args.log2n is not None else 18), 256
     x, xi = inputs.uniform_grid(N)
     plan = P.Plan.build(x, xi, eps=EPS, leaf=LEAF, kernel="fio", c_profile=0, oversample=T_OVERSAMPLE,
                         oversample_leaf=T_LEAF)
@@ -410,11 +411,12 @@ def gpu_mrhs(args, rank, world):
     st = plan.stats()
     flops = 24.0 * st["entries"] * R  # 8 real flops per complex entry and rhs, three split products
     value, tmax = job_throughput(1.0, stc, world)
-    line = {"metric": "IDBF multi-RHS applies/s at N=2^18, 256 RHS (3xTF32 tensor cores, error vs FP64 stated)",
+    lg = N.bit_length() - 1
+    line = {"metric": f"IDBF multi-RHS applies/s at N=2^{lg}, 256 RHS (3xTF32 tensor cores, error vs FP64 stated)",
             "value": value, "unit": "applies/s (256 rhs each)", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic",
-            "config": {"workload": "1D FIO N=2^18 eps=1e-6 leaf 64, 256 complex Gaussian RHS (seed 3), complex64 factors"},
+            "config": {"workload": f"1D FIO N=2^{lg} eps=1e-6 leaf 64, 256 complex Gaussian RHS (seed 3), complex64 factors"},
             "rel_err_vs_fp64": err, "vector_applies_per_s": value * R,
             "roofline": {"bound": "tensor", "achieved": flops / stc / 1e12, "unit": "TFLOP/s",
                          "peak": 1939.7 / 2, "peak_kind": "measured bf16 burst x 1/2 (nominal tf32:bf16 ratio)",
@@ -515,7 +517,7 @@ def gpu_autograd(args, rank, world):
     __graft_entry__.build()
     import paper_1809_10573_gb300 as P
     from paper_1809_10573_gb300 import inputs
-    N, R = 1 << 20, 32
+    N, R = 1 << (args.log2n if args.log2n is not None else 20), 32
     x, xi = inputs.uniform_grid(N)
     plan = P.Plan.build(x, xi, eps=EPS, leaf=LEAF, kernel="fio", c_profile=0, oversample=T_OVERSAMPLE,
                         oversample_leaf=T_LEAF)
@@ -541,11 +543,12 @@ def gpu_autograd(args, rank, world):
     torch.cuda.synchronize()
     secs = e0.elapsed_time(e1) / 1e3 / args.steps
     value, tmax = job_throughput(1.0, secs, world)
-    line = {"metric": "IDBF forward+backward steps/s at N=2^20, 32 RHS (loss ||Kx-b||^2, adjoint-butterfly backward)",
+    lg = N.bit_length() - 1
+    line = {"metric": f"IDBF forward+backward steps/s at N=2^{lg}, 32 RHS (loss ||Kx-b||^2, adjoint-butterfly backward)",
             "value": value, "unit": "fwd+bwd/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tmax * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "1D FIO N=2^20 eps=1e-6 leaf 64, 32 RHS complex64 (x seed 5, b seed 6)"},
+            "config": {"workload": f"1D FIO N=2^{lg} eps=1e-6 leaf 64, 32 RHS complex64 (x seed 5, b seed 6)"},
             "loss": float(loss.detach()), "grad_norm": float(torch.linalg.norm(g))}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -559,13 +562,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--log2n", type=int, default=20, help="N = 2^log2n (20 = the benchmarked workload)")
+    ap.add_argument("--log2n", type=int, default=None,
+                    help="N = 2^log2n (default: the benchmarked size of the workload, 20 for apply and "
+                         "autograd, 18 for mrhs; smaller cases for profiling)")
     ap.add_argument("--modes", default="df64,fp64,fp32", help="apply modes to time (df64 is the headline)")
     ap.add_argument("--workload", choices=["apply", "mrhs", "batch", "autograd"], default="apply",
                     help="apply: the headline single-vector apply at N=2^20; the others print their own lines")
     args = ap.parse_args()
     global N_LOG2
-    N_LOG2 = args.log2n
+    N_LOG2 = args.log2n if args.log2n is not None else 20
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     rank, world, local = dist_init()
