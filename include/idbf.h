@@ -147,7 +147,7 @@ idbf_status idbf_import_factors(const idbf_host_factors* f, int32_t storage, voi
 #define IDBF_MODE_DF64 1   /* DF64 storage, complex128 vectors, double-float (FP32 pair) arithmetic */
 #define IDBF_MODE_FP32 2   /* C64 storage, complex64 vectors, FP32 FMA */
 #define IDBF_MODE_TF32X3 3 /* C64 storage, complex64 vectors, 3xTF32 tensor-core block products
-                           * (tcgen05, FP32 accumulation; forward only; blocks of <= 192 rows) */
+                           * (tcgen05, FP32 accumulation; forward only; blocks of <= 256 rows) */
 
 /* idbf_apply - y = K x for an N x nrhs block: x -> V levels -> S -> U levels -> y.
  *   x, y: device pointers (may not alias), ld >= N, element type set by `mode` (above).

@@ -11,15 +11,19 @@
 //   D (128 x 2 rows):              D(n, 2r) = Re (M G)(r, n), D(n, 2r+1) = Im (M G)(r, n).
 // Split precision (3xTF32, Ootomo and Yokota, "Recovering single precision accuracy from Tensor
 // Cores while surpassing the FP32 theoretical peak performance", IJHPCA 2022): x = x_hi + x_lo with
-// x_hi = rna_tf32(x), x_lo = x - x_hi, and A B ~ A_hi B_hi + (A_hi B_lo + A_lo B_hi). The main
-// product and the two correction products go to separate TMEM accumulators (the correction terms
-// are ~2^-11 of the main ones and lose their low bits when added into the main accumulator) and
-// are summed in FP32 in the epilogue. The output rows of a block are covered in passes of at most
-// 192 real rows so that both accumulators fit in TMEM. Operands are staged by the CTA's warps
-// into shared memory in the K-major, no-swizzle canonical layout (8-row x 16-byte core
-// matrices), three stages over K with the next chunk's global loads issued before the current
-// chunk is written; one thread issues the MMAs and tcgen05.commit on an mbarrier tracks their
-// completion.
+// x_hi = rna_tf32(x), x_lo = x - x_hi, and A B ~ A_hi B_hi + (A_hi B_lo + A_lo B_hi). The tensor
+// core accumulates in FP32 with its own rounding of every addition, so the error of one long
+// accumulation grows with the number of K steps: the main products of chunk k go to one of
+// NACC = 3 TMEM accumulators (k mod 3), each of which sums a third of the terms, and the two
+// correction products (~2^-11 of the main ones, which would lose their low bits in the main
+// accumulators) to a fourth; the four are summed in round-to-nearest FP32 in the epilogue. With
+// 4 x 128 TMEM columns a pass covers 128 real (64 complex) output rows; a block takes up to four
+// passes. Eight warps stage the operands into shared memory in the K-major, no-swizzle canonical
+// layout (8-row x 16-byte core matrices), each thread writing 16 bytes (two complex columns of
+// one row) so that a warp's stores fill 512 contiguous bytes, with the global loads of the next
+// two chunks in flight; four stages over K. A ninth warp issues the MMAs as soon as a stage is
+// full (mbarrier), and tcgen05.commit frees the stage; the staging warps read the accumulators
+// out after each pass.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,20 +36,33 @@ namespace tc {
 constexpr int NT = 256;          // threads per CTA (8 warps)
 constexpr int MR = 128;          // right-hand sides per tile (MMA M)
 constexpr int KC = 8;            // complex columns per staged chunk (16 real K)
-constexpr int NH = 192;          // real output rows per pass (MMA N <= 192; two passes cover 384)
-constexpr int MAXROWS = NH;      // complex rows per block supported (2 passes x 96)
+constexpr int NH = 128;          // real output rows per pass (MMA N)
+constexpr int MAXPASS = 4;
+constexpr int MAXROWS = MAXPASS * NH / 2;  // complex rows per block supported
+constexpr int NACC = 3;          // main accumulators (chunks dealt round robin)
 constexpr uint32_t SBO = 128;    // byte step between 8-row core-matrix groups
 constexpr uint32_t A_BYTES = MR * 2 * KC * 4;     // 8 KB
-constexpr uint32_t B_BYTES = NH * 2 * KC * 4;     // 12 KB
+constexpr uint32_t B_BYTES = NH * 2 * KC * 4;     // 8 KB
 constexpr uint32_t LBO_A = (MR / 8) * 128;        // byte step between 4-element K groups
 constexpr uint32_t LBO_B = (NH / 8) * 128;
-constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;  // hi and lo of both operands: 40 KB
+constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;  // hi and lo of both operands: 32 KB
 constexpr int NSTAGE = 3;
-constexpr size_t SMEM = NSTAGE * (size_t)STAGE + 64;   // stages + barriers
+constexpr int PFR = 6;           // chunks whose global operands are in flight (cp.async raw ring)
+constexpr int RAWV = 8;          // raw complex values per thread per chunk (A: 2 items x 2, B: 2 x 2)
+constexpr uint32_t RAW_BYTES = RAWV * NT * 8;          // one raw chunk: 16 KB, value-major
+constexpr int GIXCAP = 1024;     // columns per block supported (gather indices in shared memory)
+constexpr size_t RAW_OFF = NSTAGE * (size_t)STAGE;
+constexpr size_t GIX_OFF = RAW_OFF + PFR * (size_t)RAW_BYTES;
+constexpr size_t BAR_OFF = GIX_OFF + GIXCAP * sizeof(int32_t);
+constexpr size_t SMEM = BAR_OFF + 128;                 // stages, raw ring, indices, barriers
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t D_CORR = 256;                       // TMEM column of the correction accumulator
-constexpr int A_PER_T = MR * KC / NT;                  // 4 complex A values per thread per chunk
-constexpr int B_PER_T = (NH / 2) * KC / NT;            // 3 complex B values per thread per chunk
+constexpr uint32_t D_CORR = NACC * NH;                 // TMEM column of the correction accumulator
+constexpr int A_PER_T = MR * (KC / 2) / NT;            // 2 (rhs, column pair) items per thread per chunk
+constexpr int B_PER_T = NH * (KC / 2) / NT;            // 2 (real row, column pair) items per thread per chunk
+static_assert(D_CORR + NH <= TMEM_COLS, "accumulators fit in TMEM");
+static_assert(A_PER_T * NT == MR * (KC / 2) && B_PER_T * NT == NH * (KC / 2), "whole items per thread");
+static_assert(RAWV == 2 * (A_PER_T + B_PER_T), "raw values per thread");
+static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint64_t gtimer() {
@@ -60,14 +77,6 @@ __device__ __forceinline__ bool try_wait(uint64_t* b, uint32_t parity) {
                : "r"(sa(b)), "r"(parity)
                : "memory");
   return ok != 0;
-}
-__device__ __forceinline__ bool wait_bounded(uint64_t* b, uint32_t parity, uint64_t limit_ns) {
-  if (try_wait(b, parity)) return true;
-  const uint64_t t0 = gtimer();
-  for (uint32_t n = 1;; ++n) {
-    if (try_wait(b, parity)) return true;
-    if ((n & 255) == 0 && gtimer() - t0 > limit_ns) return false;
-  }
 }
 // shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte offsets, version 1,
 // no swizzle
@@ -97,26 +106,73 @@ __device__ __forceinline__ float tf32_hi(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
-// two consecutive K elements (2k', 2k'+1) of one row: one 8-byte store per split; the lo part
-// is rounded to TF32 as well (rna) when round_lo is set, else left for the hardware to narrow
-__device__ __forceinline__ void put2(unsigned char* hi, unsigned char* lo, uint32_t off, float a, float b, int round_lo) {
-  const float ah = tf32_hi(a), bh = tf32_hi(b);
-  *(float2*)(hi + off) = make_float2(ah, bh);
-  float al = a - ah, bl = b - bh;
-  if (round_lo) { al = tf32_hi(al); bl = tf32_hi(bl); }
-  *(float2*)(lo + off) = make_float2(al, bl);
+// four consecutive K elements of one row (two complex columns): one 16-byte store per split;
+// the lo part is rounded to TF32 as well (rna) when round_lo is set, else left for the hardware
+// to narrow
+__device__ __forceinline__ void put4(unsigned char* hi, unsigned char* lo, uint32_t off, float4 v, int round_lo) {
+  const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+  *(float4*)(hi + off) = h;
+  float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+  if (round_lo) l = make_float4(tf32_hi(l.x), tf32_hi(l.y), tf32_hi(l.z), tf32_hi(l.w));
+  *(float4*)(lo + off) = l;
+}
+
+// 32 lanes x 16 consecutive 32-bit TMEM columns starting at taddr (warp-wide)
+__device__ __forceinline__ void tmem_ld16(uint32_t (&v)[16], uint32_t taddr) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+// 8-byte asynchronous copy global -> shared; src_bytes = 0 writes zeros (src is not read)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
+}
+// the staging / epilogue warps only (the MMA warp does not take part)
+__device__ __forceinline__ void staging_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }
+// bounded wait that also gives up as soon as another warp has flagged a failure
+__device__ __forceinline__ bool wait_abortable(uint64_t* b, uint32_t parity, uint64_t limit_ns, volatile int* abort_flag) {
+  if (try_wait(b, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (uint32_t n = 1;; ++n) {
+    if (try_wait(b, parity)) return true;
+    if ((n & 255) == 0 && (*abort_flag || gtimer() - t0 > limit_ns)) return false;
+  }
 }
 
 // One launch per level; persistent CTAs over nodes. x / y: user blocks (column-major, ld);
 // win / wout: workspace boundaries, element e of a segment at (off + e) * R + rhs.
-__global__ void __launch_bounds__(NT, 1)
+// Warp roles: warps 0-7 stage operands (and read the accumulators out after each pass), warp 8
+// issues the MMAs (its lane 0). Per stage s: full[s] (NT arrivals: staged), empty[s] (commit: the
+// MMAs reading it are done); per pass: done (commit: accumulators final), tfree (NT arrivals:
+// accumulators read out, the next pass may overwrite them). Every wait is bounded; on a failure a
+// thread stops waiting and working but keeps walking the same loops, so that every warp meets the
+// same named barriers, and bit 0 of *status is set.
+__global__ void __launch_bounds__(NT + 32, 1)
     k_level_tc(DevLevel d, const float2* __restrict__ mat, const float2* __restrict__ x, int64_t ldx,
                float2* __restrict__ y, int64_t ldy, const float2* __restrict__ win, float2* __restrict__ wout, int R,
                int* __restrict__ status, uint64_t limit_ns, int split_mode) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tmem_base;
-  uint64_t* bars = (uint64_t*)(sm + NSTAGE * STAGE);  // [0, NSTAGE): stage free; [NSTAGE]: pass done
+  __shared__ int abort_flag;
+  uint64_t* full = (uint64_t*)(sm + BAR_OFF);
+  float2* raw = (float2*)(sm + RAW_OFF);     // [PFR][RAWV][NT]: each thread's own values
+  int32_t* gix = (int32_t*)(sm + GIX_OFF);   // node-input element of each column of the block
+  uint64_t* empty = full + NSTAGE;
+  uint64_t* done = empty + NSTAGE;
+  uint64_t* tfree = done + 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool mma_warp = warp == NT / 32;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&tmem_base)),
                  "r"(TMEM_COLS)
@@ -124,19 +180,30 @@ __global__ void __launch_bounds__(NT, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i <= NSTAGE; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(&bars[i])), "r"(1) : "memory");
+    for (int i = 0; i < NSTAGE; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(&full[i])), "r"(NT) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(&empty[i])), "r"(1) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(done)), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(tfree)), "r"(NT) : "memory");
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  uint32_t kcg = 0, passes = 0;  // chunks and passes issued by this CTA (mbarrier phases)
+  uint32_t kcg = 0, passes = 0;  // chunks and passes so far (mbarrier phases), same on every thread
+  uint32_t issued = 0;           // chunks whose MMAs this thread committed (MMA thread)
   bool failed = false;
+  volatile int* abortp = &abort_flag;
+  auto fail = [&]() {
+    failed = true;
+    *abortp = 1;
+  };
   const int nrt = (R + MR - 1) / MR;
 
-  for (int64_t j = blockIdx.x; j < d.m && !failed; j += gridDim.x) {
+  for (int64_t j = blockIdx.x; j < d.m; j += gridDim.x) {
     int l0, l1;
     int64_t ib0 = 0;
     if (d.lev == 0) { l0 = d.n0; l1 = 0; }
@@ -160,12 +227,13 @@ __global__ void __launch_bounds__(NT, 1)
       if (d.lev == d.L) return y + (j * d.n0 + e) + (int64_t)n * ldy;
       return wout + ((e < len_o0 ? ob0 + e : ob1 + (e - len_o0)) * R + n);
     };
-    if (d.kind == KIND_U) {
+    if (d.kind == KIND_U && !mma_warp) {
       // t[q_0] = in_0 (t[p_0] comes from the block-0 products); q_1 part added with block 1
-      for (int i = tid; i < l0 * R; i += NT) *out_ptr(ix0[i / R], i % R) = in_at(i / R, i % R);
-      __syncthreads();
+      if (!failed)
+        for (int i = tid; i < l0 * R; i += NT) *out_ptr(ix0[i / R], i % R) = in_at(i / R, i % R);
+      staging_sync();
     }
-    for (int c = 0; c < 2 && !failed; ++c) {
+    for (int c = 0; c < 2; ++c) {
       const int rows = d.rows[2 * j + c], cols = d.cols[2 * j + c];
       const int32_t* ix = c ? ix1 : ix0;
       const float2* M = mat + d.moff[2 * j + c];
@@ -175,138 +243,194 @@ __global__ void __launch_bounds__(NT, 1)
         if (d.kind == KIND_U) return (c ? l0 : 0) + k;
         return k;  // S: all of concat(in_0, in_1)
       };
-      if (d.kind == KIND_U && c == 1) {
-        __syncthreads();
-        for (int i = tid; i < l1 * R; i += NT) {
-          float2* q = out_ptr(ix1[i / R], i % R);
-          const float2 a = *q, b = in_at(l0 + i / R, i % R);
-          *q = make_float2(a.x + b.x, a.y + b.y);
-        }
-        __syncthreads();
+      if (d.kind == KIND_U && c == 1 && !mma_warp) {
+        staging_sync();
+        if (!failed)
+          for (int i = tid; i < l1 * R; i += NT) {
+            float2* q = out_ptr(ix1[i / R], i % R);
+            const float2 a = *q, b = in_at(l0 + i / R, i % R);
+            *q = make_float2(a.x + b.x, a.y + b.y);
+          }
+        staging_sync();
       }
       if (rows == 0) continue;
       if (cols == 0) {  // V block that keeps every column: out = u[q]
-        for (int i = tid; i < rows * R; i += NT) {
-          const int r = i / R, n = i % R;
-          *out_ptr((c ? len_o0 : 0) + r, n) = in_at(ix[r], n);
-        }
+        if (!mma_warp && !failed)
+          for (int i = tid; i < rows * R; i += NT) {
+            const int r = i / R, n = i % R;
+            *out_ptr((c ? len_o0 : 0) + r, n) = in_at(ix[r], n);
+          }
         continue;
       }
+      if (!mma_warp) {  // column k of the block multiplies node-input element gix[k]
+        staging_sync();  // the previous block's copies are all issued
+        for (int k = tid; k < cols; k += NT) gix[k] = g_elem(k);
+        staging_sync();
+      }
       const int nkc = (cols + KC - 1) / KC;
-      const int npass = rows > NH / 2 ? 2 : 1;
-      for (int rt = 0; rt < nrt && !failed; ++rt) {
+      const int npass = (rows + NH / 2 - 1) / (NH / 2);
+      for (int rt = 0; rt < nrt; ++rt) {
         const int nr = min(MR, R - rt * MR);
-        for (int ps = 0; ps < npass && !failed; ++ps) {
+        for (int ps = 0; ps < npass; ++ps, ++passes) {
           const int r0 = ps * (NH / 2);                       // first complex row of the pass
           const int prow = min(NH / 2, rows - r0);            // complex rows of the pass
           const int nreal = (2 * prow + 15) & ~15;            // MMA N (multiple of 16)
-          // registers for one chunk's global operands (prefetched one chunk ahead)
-          float2 av[A_PER_T], bv[B_PER_T];
-          auto load = [&](int kc) {
-#pragma unroll
-            for (int t = 0; t < A_PER_T; ++t) {
-              const int i = tid + t * NT, kk = i / MR, n = i % MR, k = kc * KC + kk;
-              av[t] = (k < cols && n < nr) ? in_at(g_elem(k), rt * MR + n) : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int t = 0; t < B_PER_T; ++t) {
-              const int i = tid + t * NT, kk = i / (NH / 2), r = i % (NH / 2), k = kc * KC + kk;
-              bv[t] = (k < cols && r < prow) ? M[(int64_t)k * rows + r0 + r] : make_float2(0.f, 0.f);
-            }
-          };
-          load(0);
-          for (int kc = 0; kc < nkc; ++kc, ++kcg) {
-            const int s = kcg % NSTAGE;
-            unsigned char* Ah = sm + (size_t)s * STAGE;
-            unsigned char* Al = Ah + A_BYTES;
-            unsigned char* Bh = Al + A_BYTES;
-            unsigned char* Bl = Bh + B_BYTES;
-            // the MMAs that last read stage s must be done
-            if (!wait_bounded(&bars[s], ((kcg / NSTAGE) & 1) ^ 1, limit_ns)) { failed = true; break; }
-#pragma unroll
-            for (int t = 0; t < A_PER_T; ++t) {
-              const int i = tid + t * NT, kk = i / MR, n = i % MR;
-              put2(Ah, Al, koff(n, 2 * kk, LBO_A), av[t].x, av[t].y, split_mode >= 1);
-            }
-#pragma unroll
-            for (int t = 0; t < B_PER_T; ++t) {
-              const int i = tid + t * NT, kk = i / (NH / 2), r = i % (NH / 2);
-              put2(Bh, Bl, koff(2 * r, 2 * kk, LBO_B), bv[t].x, -bv[t].y, split_mode >= 1);
-              put2(Bh, Bl, koff(2 * r + 1, 2 * kk, LBO_B), bv[t].y, bv[t].x, split_mode >= 1);
-            }
-            if (kc + 1 < nkc) load(kc + 1);  // in flight while this chunk's MMAs run
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (mma_warp) {
+            if (lane == 0) {
+              // the previous pass's accumulators must have been read out
+              if (!failed && passes > 0 && !wait_abortable(tfree, (passes - 1) & 1, limit_ns, abortp)) fail();
               const uint32_t id = idesc_tf32((uint32_t)nreal, MR);
-              for (int ks = 0; ks < 2; ++ks) {  // K = 8 real per MMA: two 4-element core groups
-                const uint32_t ao = 2 * ks * LBO_A, bo = 2 * ks * LBO_B;
-                const uint64_t ah = sdesc(sa(Ah) + ao, LBO_A, SBO), al = sdesc(sa(Al) + ao, LBO_A, SBO);
-                const uint64_t bh = sdesc(sa(Bh) + bo, LBO_B, SBO), bl = sdesc(sa(Bl) + bo, LBO_B, SBO);
-                const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
-                mma_tf32(tmem, ah, bh, id, first);             // main: hi * hi
-                mma_tf32(tmem + D_CORR, ah, bl, id, first);    // corrections: hi * lo + lo * hi
-                mma_tf32(tmem + D_CORR, al, bh, id, 1u);
-                if (split_mode == 2) mma_tf32(tmem + D_CORR, al, bl, id, 1u);
-              }
-              commit(&bars[s]);
-              if (kc == nkc - 1) commit(&bars[NSTAGE]);
-            }
-          }
-          if (failed) break;
-          // epilogue: lane quadrant of warp w % 4 = 32 rhs; warps w and w + 4 split the columns
-          if (!wait_bounded(&bars[NSTAGE], passes & 1, limit_ns)) { failed = true; break; }
-          ++passes;
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int q = warp & 3, half = warp >> 2;
-          const int n = rt * MR + q * 32 + lane;
-          for (int c0 = half * 16; c0 < nreal; c0 += 32) {
-            uint32_t v[16], w[16];
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(taddr));
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]),
-                  "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]), "=r"(w[15])
-                : "r"(taddr + D_CORR));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (n >= R) continue;
+              for (int kc = 0; kc < nkc; ++kc) {
+                const uint32_t g = kcg + (uint32_t)kc;
+                const int s = (int)(g % NSTAGE);
+                if (failed) continue;
+                if (!wait_abortable(&full[s], (g / NSTAGE) & 1, limit_ns, abortp)) { fail(); continue; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t Ah = sa(sm + (size_t)s * STAGE), Al = Ah + A_BYTES, Bh = Al + A_BYTES, Bl = Bh + B_BYTES;
+                const uint32_t dmain = tmem + (uint32_t)(kc % NACC) * NH;
 #pragma unroll
-            for (int h = 0; h < 8; ++h) {
-              const int r = r0 + (c0 >> 1) + h;  // complex output row of the block
-              if ((c0 >> 1) + h >= prow) break;
-              const float2 res = make_float2(__uint_as_float(v[2 * h]) + __uint_as_float(w[2 * h]),
-                                             __uint_as_float(v[2 * h + 1]) + __uint_as_float(w[2 * h + 1]));
-              if (d.kind == KIND_V) {
-                const float2 uq = in_at(ix[r], n);
-                *out_ptr((c ? len_o0 : 0) + r, n) = make_float2(res.x + uq.x, res.y + uq.y);
-              } else if (d.kind == KIND_S) {
-                *out_ptr((c ? len_o0 : 0) + r, n) = res;
-              } else {
-                float2* p = out_ptr(ix[(c ? l1 : l0) + r], n);
-                if (c == 0) *p = res;
-                else { const float2 a = *p; *p = make_float2(a.x + res.x, a.y + res.y); }
+                for (int ks = 0; ks < 2; ++ks) {  // K = 8 real per MMA: two 4-element core groups
+                  const uint32_t ao = 2 * ks * LBO_A, bo = 2 * ks * LBO_B;
+                  const uint64_t ah = sdesc(Ah + ao, LBO_A, SBO), al = sdesc(Al + ao, LBO_A, SBO);
+                  const uint64_t bh = sdesc(Bh + bo, LBO_B, SBO), bl = sdesc(Bl + bo, LBO_B, SBO);
+                  const uint32_t first_main = (kc < NACC && ks == 0) ? 0u : 1u;
+                  const uint32_t first_corr = (kc == 0 && ks == 0) ? 0u : 1u;
+                  mma_tf32(dmain, ah, bh, id, first_main);            // main: hi * hi
+                  mma_tf32(tmem + D_CORR, ah, bl, id, first_corr);    // corrections: hi * lo + lo * hi
+                  mma_tf32(tmem + D_CORR, al, bh, id, 1u);
+                  if (split_mode == 2) mma_tf32(tmem + D_CORR, al, bl, id, 1u);
+                }
+                commit(&empty[s]);
+                ++issued;
+                if (kc == nkc - 1) commit(done);
+              }
+            }
+            kcg += (uint32_t)nkc;
+            continue;
+          }
+          // ---- staging warps: each thread copies (cp.async, PFR chunks ahead) exactly the values
+          // it later converts, into its own slots of the raw ring, so no barrier is needed
+          // between the copies and their use. Items: (right-hand side n or real row rr, pair of
+          // complex columns), four real K each.
+          auto issue_raw = [&](int kc) {
+            if (kc < nkc && !failed) {
+              float2* rs = raw + (size_t)(kc % PFR) * (RAWV * NT) + tid;
+#pragma unroll
+              for (int t = 0; t < A_PER_T; ++t) {
+                const int i = tid + t * NT, n = i % MR, k = kc * KC + 2 * (i / MR);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const bool ok = n < nr && k + h < cols;
+                  const int e = ok ? gix[k + h] : 0;
+                  const float2* src = !ok ? M
+                                      : d.lev == 0 ? x + (j * d.n0 + e) + (int64_t)(rt * MR + n) * ldx
+                                                   : win + (ib0 + e) * R + rt * MR + n;
+                  cp_async8(rs + (2 * t + h) * NT, src, ok ? 8u : 0u);
+                }
+              }
+#pragma unroll
+              for (int t = 0; t < B_PER_T; ++t) {
+                const int i = tid + t * NT, rr = i % NH, k = kc * KC + 2 * (i / NH), r = rr >> 1;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const bool ok = r < prow && k + h < cols;
+                  const float2* src = ok ? M + (int64_t)(k + h) * rows + r0 + r : M;
+                  cp_async8(rs + (2 * A_PER_T + 2 * t + h) * NT, src, ok ? 8u : 0u);
+                }
+              }
+            }
+            cp_async_commit();  // one group per chunk (empty past the end), so that the counts match
+          };
+#pragma unroll
+          for (int f = 0; f < PFR; ++f) issue_raw(f);
+          for (int kc = 0; kc < nkc; ++kc) {
+            const uint32_t g = kcg + (uint32_t)kc;
+            const int s = (int)(g % NSTAGE);
+            cp_async_wait<PFR - 1>();  // this thread's copies of chunk kc have landed
+            // the MMAs that last read stage s must be done
+            if (!failed && !wait_abortable(&empty[s], ((g / NSTAGE) & 1) ^ 1, limit_ns, abortp)) fail();
+            if (!failed) {
+              const float2* rs = raw + (size_t)(kc % PFR) * (RAWV * NT) + tid;
+              unsigned char* Ah = sm + (size_t)s * STAGE;
+              unsigned char* Al = Ah + A_BYTES;
+              unsigned char* Bh = Al + A_BYTES;
+              unsigned char* Bl = Bh + B_BYTES;
+#pragma unroll
+              for (int t = 0; t < A_PER_T; ++t) {
+                const int i = tid + t * NT;
+                const float2 g0 = rs[(2 * t) * NT], g1 = rs[(2 * t + 1) * NT];
+                put4(Ah, Al, koff(i % MR, 4 * (i / MR), LBO_A), make_float4(g0.x, g0.y, g1.x, g1.y), split_mode >= 1);
+              }
+#pragma unroll
+              for (int t = 0; t < B_PER_T; ++t) {
+                const int i = tid + t * NT, rr = i % NH;
+                const float2 m0 = rs[(2 * A_PER_T + 2 * t) * NT], m1 = rs[(2 * A_PER_T + 2 * t + 1) * NT];
+                // real row 2r holds (Re M, -Im M) per column, real row 2r+1 (Im M, Re M)
+                const float4 bv = (rr & 1) ? make_float4(m0.y, m0.x, m1.y, m1.x) : make_float4(m0.x, -m0.y, m1.x, -m1.y);
+                put4(Bh, Bl, koff(rr, 4 * (i / NH), LBO_B), bv, split_mode >= 1);
+              }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&full[s]);
+            issue_raw(kc + PFR);  // into the slot just consumed
+          }
+          cp_async_wait<0>();
+          kcg += (uint32_t)nkc;
+          // ---- epilogue: lane quadrant of warp w % 4 = 32 rhs; warps w and w + 4 split the columns
+          if (!failed && !wait_abortable(done, passes & 1, limit_ns, abortp)) fail();
+          if (__any_sync(0xffffffffu, failed)) failed = true;  // warp-uniform from here (tcgen05.ld)
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (!failed) {
+            const int q = warp & 3, half = warp >> 2;
+            const int n = rt * MR + q * 32 + lane;
+            const int nacc = min(NACC, nkc);  // main accumulators written in this pass
+            for (int c0 = half * 16; c0 < nreal; c0 += 32) {
+              const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+              uint32_t v[16], w[16];
+              float acc[16];
+              tmem_ld16(v, taddr);
+              tmem_ld16(w, taddr + D_CORR);
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+              for (int e = 0; e < 16; ++e) acc[e] = __uint_as_float(v[e]);
+              for (int a = 1; a < nacc; ++a) {  // the other main accumulators, in order
+                tmem_ld16(v, taddr + (uint32_t)a * NH);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int e = 0; e < 16; ++e) acc[e] += __uint_as_float(v[e]);
+              }
+#pragma unroll
+              for (int e = 0; e < 16; ++e) acc[e] += __uint_as_float(w[e]);
+              if (n >= R) continue;
+#pragma unroll
+              for (int h = 0; h < 8; ++h) {
+                const int r = r0 + (c0 >> 1) + h;  // complex output row of the block
+                if ((c0 >> 1) + h >= prow) break;
+                const float2 res = make_float2(acc[2 * h], acc[2 * h + 1]);
+                if (d.kind == KIND_V) {
+                  const float2 uq = in_at(ix[r], n);
+                  *out_ptr((c ? len_o0 : 0) + r, n) = make_float2(res.x + uq.x, res.y + uq.y);
+                } else if (d.kind == KIND_S) {
+                  *out_ptr((c ? len_o0 : 0) + r, n) = res;
+                } else {
+                  float2* pp = out_ptr(ix[(c ? l1 : l0) + r], n);
+                  if (c == 0) *pp = res;
+                  else { const float2 a = *pp; *pp = make_float2(a.x + res.x, a.y + res.y); }
+                }
               }
             }
           }
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          __syncthreads();  // TMEM read out before the next pass's MMAs overwrite it
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          mbar_arrive(tfree);  // the next pass's MMAs may overwrite the accumulators
         }
       }
     }
-    __syncthreads();
   }
-  if (failed && (tid & 31) == 0) atomicOr(status, 1);
-  // the last MMAs must have completed before the accumulators are released
-  if (tid == 0 && kcg > 0) {
+  if (failed && lane == 0) atomicOr(status, 1);
+  // the last MMAs must have completed before the accumulators and stages are released
+  if (mma_warp && lane == 0 && issued > 0) {
     const uint64_t t0 = gtimer();
-    while (!try_wait(&bars[(kcg - 1) % NSTAGE], ((kcg - 1) / NSTAGE) & 1) && gtimer() - t0 < limit_ns) {
+    while (!try_wait(&empty[(issued - 1) % NSTAGE], ((issued - 1) / NSTAGE) & 1) && gtimer() - t0 < limit_ns) {
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -319,7 +443,7 @@ __global__ void __launch_bounds__(NT, 1)
 // the 3xTF32 apply of all levels (forward); returns EUNSUPPORTED if a block is too large
 idbf_status apply_tf32x3(Plan* p, const void* x, void* y, int64_t R, int64_t ld, cudaStream_t st) {
   for (int l = 0; l <= p->L; ++l)
-    if (p->lv[l].max_rows > tc::MAXROWS) return IDBF_EUNSUPPORTED;
+    if (p->lv[l].max_rows > tc::MAXROWS || p->lv[l].max_cols > tc::GIXCAP) return IDBF_EUNSUPPORTED;
   IDBF_CUDA_TRY(cudaFuncSetAttribute(tc::k_level_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM));
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -332,7 +456,7 @@ idbf_status apply_tf32x3(Plan* p, const void* x, void* y, int64_t R, int64_t ld,
     const float2* win = l > 0 ? wb[(l - 1) & 1] : nullptr;
     float2* wout = l < p->L ? wb[l & 1] : nullptr;
     const unsigned ctas = (unsigned)std::min<int64_t>(p->m, sms);
-    tc::k_level_tc<<<ctas, tc::NT, tc::SMEM, st>>>(d, (const float2*)p->lmat[IDBF_STORE_C64][l], (const float2*)x, ld,
+    tc::k_level_tc<<<ctas, tc::NT + 32, tc::SMEM, st>>>(d, (const float2*)p->lmat[IDBF_STORE_C64][l], (const float2*)x, ld,
                                                   (float2*)y, ld, win, wout, (int)R, p->d_status, p->wait_limit_ns,
                                                   p->tc_split_mode);
     IDBF_CUDA_TRY(cudaGetLastError());

@@ -48,3 +48,21 @@ def test_tf32x3_adjoint_is_refused():
     xd = torch.zeros((c["N"], 2), dtype=torch.complex64, device="cuda")
     with pytest.raises(P.IDBFError):
         plan.apply_adjoint(xd, mode=P.MODE_TF32X3)
+
+
+def test_tf32x3_tall_blocks_within_the_split_precision_bar():
+    """GPU-built FIO at N = 2^16, eps = 1e-6: blocks of up to ~184 rows take three 64-row passes,
+    and 160 right-hand sides two M tiles (the second ragged). The split-precision form must stay
+    within 1e-6 + eps of the FP64 apply; against the FP64 apply of the same factors (eps does not
+    enter) the test asks for 2e-6."""
+    N = 1 << 16
+    x, xi = inputs.uniform_grid(N)
+    plan = P.Plan.build(x, xi, eps=1e-6, leaf=64, kernel="fio", c_profile=0, oversample=2, oversample_leaf=4)
+    assert max(plan.stats()["level_kmax"]) > 128
+    plan.set_storage(P.STORE_C128, P.STORE_C64)
+    X = inputs.complex_gaussian(N, 160, seed=82)
+    y64 = plan.apply(torch.from_numpy(X).cuda(), mode=P.MODE_FP64).cpu().numpy()
+    ytc = plan.apply(torch.from_numpy(X.astype(np.complex64)).cuda(), mode=P.MODE_TF32X3)
+    plan.sync_status()
+    err = rel(ytc.cpu().numpy(), y64)
+    assert err < 2e-6, err
