@@ -202,6 +202,16 @@ __global__ void __launch_bounds__(NT + 32, 1)
     *abortp = 1;
   };
   const int nrt = (R + MR - 1) / MR;
+  // this thread's staging items (the same in every chunk): A items (rhs n, column pair kp),
+  // B items (real row rr, column pair kp); NT = 2 MR = 2 NH, so n = rr = tid % 128
+  static_assert(NT == 2 * MR && NT == 2 * NH && A_PER_T == 2 && B_PER_T == 2, "item map");
+  const int it_n = tid & (MR - 1), it_kp0 = tid >> 7;  // items t = 0, 1: column pairs kp0, kp0 + 2
+  uint32_t offA[2], offB[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    offA[t] = koff(it_n, 4 * (it_kp0 + 2 * t), LBO_A);
+    offB[t] = koff(it_n, 4 * (it_kp0 + 2 * t), LBO_B);
+  }
 
   for (int64_t j = blockIdx.x; j < d.m; j += gridDim.x) {
     int l0, l1;
@@ -312,32 +322,25 @@ __global__ void __launch_bounds__(NT + 32, 1)
           // it later converts, into its own slots of the raw ring, so no barrier is needed
           // between the copies and their use. Items: (right-hand side n or real row rr, pair of
           // complex columns), four real K each.
+          // where this thread's values of column k live: A: a_base + gix[k] * a_step (node input
+          // element gix[k], right-hand side rt*MR + it_n); B: b_base + k * rows (block row r0 + it_n/2)
+          const bool okA = it_n < nr, okB = (it_n >> 1) < prow;
+          const float2* a_base = d.lev == 0 ? x + j * d.n0 + (int64_t)(rt * MR + it_n) * ldx : win + ib0 * R + rt * MR + it_n;
+          const int64_t a_step = d.lev == 0 ? 1 : R;
+          const float2* b_base = M + r0 + (it_n >> 1);
           auto issue_raw = [&](int kc) {
             if (kc < nkc && !failed) {
               float2* rs = raw + (size_t)(kc % PFR) * (RAWV * NT) + tid;
 #pragma unroll
-              for (int t = 0; t < A_PER_T; ++t) {
-                const int i = tid + t * NT, n = i % MR, k = kc * KC + 2 * (i / MR);
+              for (int t = 0; t < 2; ++t)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                  const bool ok = n < nr && k + h < cols;
-                  const int e = ok ? gix[k + h] : 0;
-                  const float2* src = !ok ? M
-                                      : d.lev == 0 ? x + (j * d.n0 + e) + (int64_t)(rt * MR + n) * ldx
-                                                   : win + (ib0 + e) * R + rt * MR + n;
-                  cp_async8(rs + (2 * t + h) * NT, src, ok ? 8u : 0u);
+                  const int k = kc * KC + 2 * (it_kp0 + 2 * t) + h;
+                  const bool inb = k < cols;
+                  const bool oa = okA && inb, ob = okB && inb;
+                  cp_async8(rs + (2 * t + h) * NT, oa ? a_base + gix[k] * a_step : M, oa ? 8u : 0u);
+                  cp_async8(rs + (4 + 2 * t + h) * NT, ob ? b_base + (int64_t)k * rows : M, ob ? 8u : 0u);
                 }
-              }
-#pragma unroll
-              for (int t = 0; t < B_PER_T; ++t) {
-                const int i = tid + t * NT, rr = i % NH, k = kc * KC + 2 * (i / NH), r = rr >> 1;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                  const bool ok = r < prow && k + h < cols;
-                  const float2* src = ok ? M + (int64_t)(k + h) * rows + r0 + r : M;
-                  cp_async8(rs + (2 * A_PER_T + 2 * t + h) * NT, src, ok ? 8u : 0u);
-                }
-              }
             }
             cp_async_commit();  // one group per chunk (empty past the end), so that the counts match
           };
@@ -356,18 +359,13 @@ __global__ void __launch_bounds__(NT + 32, 1)
               unsigned char* Bh = Al + A_BYTES;
               unsigned char* Bl = Bh + B_BYTES;
 #pragma unroll
-              for (int t = 0; t < A_PER_T; ++t) {
-                const int i = tid + t * NT;
+              for (int t = 0; t < 2; ++t) {
                 const float2 g0 = rs[(2 * t) * NT], g1 = rs[(2 * t + 1) * NT];
-                put4(Ah, Al, koff(i % MR, 4 * (i / MR), LBO_A), make_float4(g0.x, g0.y, g1.x, g1.y), split_mode >= 1);
-              }
-#pragma unroll
-              for (int t = 0; t < B_PER_T; ++t) {
-                const int i = tid + t * NT, rr = i % NH;
-                const float2 m0 = rs[(2 * A_PER_T + 2 * t) * NT], m1 = rs[(2 * A_PER_T + 2 * t + 1) * NT];
+                put4(Ah, Al, offA[t], make_float4(g0.x, g0.y, g1.x, g1.y), split_mode >= 1);
+                const float2 m0 = rs[(4 + 2 * t) * NT], m1 = rs[(4 + 2 * t + 1) * NT];
                 // real row 2r holds (Re M, -Im M) per column, real row 2r+1 (Im M, Re M)
-                const float4 bv = (rr & 1) ? make_float4(m0.y, m0.x, m1.y, m1.x) : make_float4(m0.x, -m0.y, m1.x, -m1.y);
-                put4(Bh, Bl, koff(rr, 4 * (i / NH), LBO_B), bv, split_mode >= 1);
+                const float4 bv = (it_n & 1) ? make_float4(m0.y, m0.x, m1.y, m1.x) : make_float4(m0.x, -m0.y, m1.x, -m1.y);
+                put4(Bh, Bl, offB[t], bv, split_mode >= 1);
               }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
