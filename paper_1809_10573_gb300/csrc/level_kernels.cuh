@@ -464,7 +464,7 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
 //     own after a barrier (every output position receives exactly one term from each block, so
 //     the order of the two additions does not change the sum).
 namespace tiled {
-constexpr int TR = 4, KC = 8, STAGES = 3;
+constexpr int TR = 4, KC = 16, STAGES = 2;
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
