@@ -583,10 +583,29 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
 }
 
 // ---------------------------------------------------------------------------------------------
+// Warp-per-node forward level kernel (one right-hand side, short blocks): warp w of the grid
+// takes nodes w, w + W, ... (fwd_node_warp in level_kernels.cuh).
+constexpr int kWarpNodeWarps = 8;  // warps per CTA
+template <class P, int RPL>
+__global__ void __launch_bounds__(kWarpNodeWarps * 32) k_level_warp(DevLevel d, const typename P::mat_t* __restrict__ mat,
+                                                                   IO<typename P::vec_t> io, int max_in, int gcap,
+                                                                   int max_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int w = threadIdx.x >> 5;
+  unsigned char* wsm = smem + (size_t)w * warp_node_smem<P>(max_in, gcap, max_out);
+  const int64_t nw = (int64_t)gridDim.x * kWarpNodeWarps;
+  for (int64_t j = (int64_t)blockIdx.x * kWarpNodeWarps + w; j < d.m; j += nw) {
+    fwd_node_warp<P, RPL>(d, mat, io, max_in, gcap, j, wsm);
+    __syncwarp();  // the next node's inputs overwrite this node's shared memory
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Forward level kernels for one right-hand side. Variant 0: the per-node kernel; variants
 // 1..6: the streaming kernel with ring layout A, B or C (see strm::Ring*), each with the node
-// inputs copied by the producer (odd variants) or loaded by the consumers (even variants).
-constexpr int kNumFwdVariants = 7;
+// inputs copied by the producer (odd variants) or loaded by the consumers (even variants);
+// variant 7: the warp-per-node kernel (levels whose blocks have at most 128 rows).
+constexpr int kNumFwdVariants = 8;
 
 static int default_variant(int fmt) { return fmt == IDBF_STORE_C128 ? 0 : 1; }
 
@@ -625,13 +644,35 @@ static idbf_status launch_stream(Plan* p, int l, bool bulk, const void* x, IO<ty
 }
 
 template <class P>
+static idbf_status launch_warp_node(Plan* p, int l, IO<typename P::vec_t> io, cudaStream_t st, int fmt) {
+  const LevelInfo& li = p->lv[l];
+  const int gcap = std::max(li.max_cols, li.max_in);
+  const size_t per = warp_node_smem<P>(li.max_in, gcap, li.max_out);
+  if (li.max_rows > 128 || per > 24 * 1024) return IDBF_EUNSUPPORTED;
+  const size_t sm = per * kWarpNodeWarps;
+  const DevLevel d = p->level(l);
+  const typename P::mat_t* mat = (const typename P::mat_t*)p->lmat[fmt][l];
+  const unsigned grid = (unsigned)((p->m + kWarpNodeWarps - 1) / kWarpNodeWarps);
+  auto go = [&](auto kern) -> idbf_status {
+    if (sm > 48 * 1024) IDBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    kern<<<grid, kWarpNodeWarps * 32, sm, st>>>(d, mat, io, li.max_in, gcap, li.max_out);
+    IDBF_CUDA_TRY(cudaGetLastError());
+    return IDBF_OK;
+  };
+  if (li.max_rows <= 32) return go(k_level_warp<P, 1>);
+  if (li.max_rows <= 64) return go(k_level_warp<P, 2>);
+  return go(k_level_warp<P, 4>);
+}
+
+template <class P>
 static idbf_status launch_fwd_variant(Plan* p, int l, int v, const void* x, void* y, const typename P::vec_t* win,
                                       typename P::vec_t* wout, cudaStream_t st, int fmt) {
   using V = typename P::vec_t;
   IO<V> io;
   io.x = (const V*)x; io.ldx = p->N; io.y = (V*)y; io.ldy = p->N; io.R = 1;
   io.win = win; io.wout = wout;
-  if (v != 0 && fmt == IDBF_STORE_C128) return IDBF_EUNSUPPORTED;  // FP64: per-node kernel only
+  if (v == 7) return launch_warp_node<P>(p, l, io, st, fmt);
+  if (v != 0 && fmt == IDBF_STORE_C128) return IDBF_EUNSUPPORTED;  // FP64: per-node or warp-per-node kernel
   switch (v) {
     case 1: return launch_stream<P, strm::RingA>(p, l, true, x, io, st);
     case 2: return launch_stream<P, strm::RingA>(p, l, false, x, io, st);

@@ -727,4 +727,144 @@ __device__ __forceinline__ void fwd_node_tiled(const DevLevel& d, const typename
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------------------------------------
+// Warp-per-node forward body, one right-hand side, for levels of short blocks (the outer levels
+// of the butterfly: leaves and their neighbours). Every phase of a node (inputs, gathered operands,
+// block products, combination) is done by one warp with __syncwarp between phases, so a CTA has
+// as many nodes in flight as it has warps and no phase waits for another warp. Lanes cover the
+// rows of a block, RPL rows each (rows <= 32 RPL); a column of a block is read by the warp as
+// consecutive entries. Shared memory per warp: u[max_in] (inputs), g[2][gcap] (gathered
+// operands), t[max_out] (row-ID accumulation of a U level).
+template <class P>
+__host__ __device__ constexpr size_t warp_node_smem(int max_in, int gcap, int max_out) {
+  return (((size_t)max_in * sizeof(typename P::vec_t) + 2 * (size_t)gcap * sizeof(typename P::gv_t) +
+           (size_t)max_out * sizeof(typename P::vec_t)) + 15) & ~(size_t)15;
+}
+
+template <class P, int RPL>
+__device__ __forceinline__ void fwd_node_warp(const DevLevel& d, const typename P::mat_t* __restrict__ mat,
+                                              const IO<typename P::vec_t>& io, int max_in, int gcap, int64_t j,
+                                              unsigned char* wsm) {
+  using V = typename P::vec_t;
+  using G = typename P::gv_t;
+  using M = typename P::mat_t;
+  V* u = (V*)wsm;
+  G* g = (G*)(u + max_in);
+  V* t = (V*)(g + 2 * (size_t)gcap);
+  const int lane = threadIdx.x & 31;
+
+  // inputs -> u
+  int l0, l1;
+  if (d.lev == 0) {
+    l0 = d.n0;
+    l1 = 0;
+    for (int e = lane; e < l0; e += 32) u[e] = io.x[j * d.n0 + e];
+  } else {
+    l0 = d.in_len[2 * j];
+    l1 = d.in_len[2 * j + 1];
+    const int64_t o0 = d.in_off[2 * j], o1 = d.in_off[2 * j + 1];
+    for (int e = lane; e < l0 + l1; e += 32) u[e] = io.win[(e < l0 ? o0 + e : o1 + (e - l0)) * io.R];
+  }
+  const int rowsv[2] = {d.rows[2 * j], d.rows[2 * j + 1]};
+  const int colsv[2] = {d.cols[2 * j], d.cols[2 * j + 1]};
+  const int64_t mov[2] = {d.moff[2 * j], d.moff[2 * j + 1]};
+  const int32_t* ixv[2] = {d.idx + d.ioff[2 * j], d.idx + d.ioff[2 * j + 1]};
+  __syncwarp();
+
+  // gathered operands -> g
+  if (d.kind == KIND_V) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      for (int k = lane; k < colsv[c]; k += 32) g[c * gcap + k] = P::cvt(u[ixv[c][rowsv[c] + k]]);
+  } else if (d.kind == KIND_S) {
+    for (int e = lane; e < l0 + l1; e += 32) g[e] = P::cvt(u[e]);
+  } else {
+    for (int e = lane; e < l0; e += 32) g[e] = P::cvt(u[e]);
+    for (int e = lane; e < l1; e += 32) g[gcap + e] = P::cvt(u[l0 + e]);
+  }
+  __syncwarp();
+
+  // block products: lane owns rows lane + 32 i
+  V res[2][RPL];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int rows = rowsv[c], cols = colsv[c];
+    const M* Mc = mat + mov[c];
+    const G* gc = g + (d.kind == KIND_S ? 0 : c * gcap);
+    typename P::acc_t acc[RPL];
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) P::init(acc[i]);
+    int k = 0;
+    for (; k + P::CHUNK <= cols; k += P::CHUNK) {
+#pragma unroll 8
+      for (int q = 0; q < P::CHUNK; ++q) {
+        const G gv = gc[k + q];
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+          const int r = lane + 32 * i;
+          if (r < rows) P::mac(acc[i], P::ld(Mc + (int64_t)(k + q) * rows + r), gv);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) P::flush(acc[i]);
+    }
+    for (; k < cols; ++k) {
+      const G gv = gc[k];
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        if (r < rows) P::mac(acc[i], P::ld(Mc + (int64_t)k * rows + r), gv);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+      P::flush(acc[i]);
+      res[c][i] = P::fin(acc[i]);
+    }
+    if (d.kind != KIND_U) {
+      const int64_t ob = d.out_off[out_seg_id(d, j, c)];
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        if (r >= rows) continue;
+        V v = res[c][i];
+        if (d.kind == KIND_V) v = P::add(v, u[ixv[c][r]]);
+        io.wout[(ob + r) * io.R] = v;
+      }
+    }
+  }
+  if (d.kind != KIND_U) return;
+  // row-ID level: t[q_c] = in_c, t[p_c] = res_c, block 0 first (q_0, p_0 partition t), then
+  // block 1 adds (q_1, p_1 also a partition)
+  const int tl = l0 + rowsv[0];
+  for (int e = lane; e < l0; e += 32) t[ixv[0][e]] = u[e];
+#pragma unroll
+  for (int i = 0; i < RPL; ++i) {
+    const int r = lane + 32 * i;
+    if (r < rowsv[0]) t[ixv[0][l0 + r]] = res[0][i];
+  }
+  __syncwarp();
+  for (int e = lane; e < l1; e += 32) {
+    V* dst = &t[ixv[1][e]];
+    *dst = P::add(*dst, u[l0 + e]);
+  }
+#pragma unroll
+  for (int i = 0; i < RPL; ++i) {
+    const int r = lane + 32 * i;
+    if (r < rowsv[1]) {
+      V* dst = &t[ixv[1][l1 + r]];
+      *dst = P::add(*dst, res[1][i]);
+    }
+  }
+  __syncwarp();
+  if (d.lev == d.L) {
+    for (int e = lane; e < tl; e += 32) io.y[j * d.n0 + e] = t[e];
+  } else {
+    const int64_t s0 = out_seg_id(d, j, 0), s1 = out_seg_id(d, j, 1);
+    const int len0 = d.out_len[s0];
+    const int64_t b0 = d.out_off[s0], b1 = d.out_off[s1];
+    for (int e = lane; e < tl; e += 32) io.wout[(e < len0 ? b0 + e : b1 + (e - len0)) * io.R] = t[e];
+  }
+}
+
 }  // namespace idbf

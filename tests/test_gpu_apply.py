@@ -153,16 +153,17 @@ def test_bounded_waits_report_a_timeout_and_the_context_survives():
 
 
 @pytest.mark.parametrize("case", ["fio_base_8192_oddL", "dft_jit_2048_oddL"])
-@pytest.mark.parametrize("mode,fmt,tol", [(P.MODE_DF64, P.STORE_DF64, 1e-12), (P.MODE_FP32, P.STORE_C64, 2e-5)])
+@pytest.mark.parametrize("mode,fmt,tol", [(P.MODE_DF64, P.STORE_DF64, 1e-12), (P.MODE_FP32, P.STORE_C64, 2e-5),
+                                          (P.MODE_FP64, P.STORE_C128, 1e-12)])
 def test_every_forward_variant_matches_oracle(case, mode, fmt, tol):
     # the autotuner may pick any variant on any level: each must give the oracle's result
     c, plan = _plan(case)
     plan.set_storage(fmt)
     X = inputs.complex_gaussian(c["N"], 1, seed=41)
-    dt = torch.complex128 if mode == P.MODE_DF64 else torch.complex64
+    dt = torch.complex64 if mode == P.MODE_FP32 else torch.complex128
     xd = torch.from_numpy(X).to(dt).cuda()
     ref = idbf.apply(c["F"], X)
-    for v in range(7):
+    for v in range(8):   # FP64 runs variants 0 and 7; the streaming ones fall back to 0
         plan.set_level_variants(mode, [v] * (c["F"].L + 1))
         y = plan.apply(xd, mode=mode)
         plan.sync_status()
@@ -170,5 +171,5 @@ def test_every_forward_variant_matches_oracle(case, mode, fmt, tol):
     ms = plan.autotune(mode, reps=2)
     assert ms > 0
     chosen = plan.stats()["level_variant"][fmt]
-    assert all(0 <= v < 7 for v in chosen)
+    assert all(0 <= v < 8 for v in chosen)
     assert rel(plan.apply(xd, mode=mode).cpu().numpy(), ref) < tol
