@@ -42,6 +42,18 @@ __global__ void __launch_bounds__(256, MINB) k_level_fwd_tiled(DevLevel d, const
                               (int)(blockIdx.x % nblk) * RB, smem);
 }
 
+// Several right-hand sides, FP32 / FP64 adjoint (adj_node_tiled): node blockIdx.x / nblk,
+// right-hand-side block blockIdx.x % nblk.
+template <class P, int RB, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_level_adj_tiled(DevLevel d, const typename P::mat_t* __restrict__ mat,
+                                                               IO<typename P::vec_t> io, int max_in, int max_out,
+                                                               int max_rows, int max_cols, int nblk) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if constexpr (tiled_ok<P>())
+    adj_node_tiled<P, RB>(d, mat, io, max_in, max_out, max_rows, max_cols, (int64_t)(blockIdx.x / nblk),
+                          (int)(blockIdx.x % nblk) * RB, smem);
+}
+
 // ---------------------------------------------------------------------------------------------
 // adjoint level kernel: reads the forward outputs of node j, writes its forward inputs.
 // Shared memory: v[max_out][RB], g[2][gcap][RB], res[2][rcap][RB], ub[max_in][RB].
@@ -780,6 +792,20 @@ static idbf_status run_levels(Plan* p, const void* x, void* y, int64_t R, int64_
         IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_fwd<P, RB, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       k_level_fwd<P, RB, RPT><<<grid, NT, sm, st>>>(d, mat, io, gcap, rcap, li.max_in);
     } else {
+      if constexpr (RB >= 8 && tiled_ok<P>()) {
+        // several right-hand sides, FP32 / FP64: register tiles over streamed row chunks
+        const size_t sm = tadj::smem_bytes<P, RB>(li.max_in, li.max_out, li.max_rows, li.max_cols);
+        if (sm <= 200 * 1024) {
+          constexpr bool f32 = sizeof(V) == 8;
+          auto kern = k_level_adj_tiled<P, RB, f32 ? 2 : 1>;
+          if (sm > 48 * 1024) IDBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+          const int nblk = (int)((R + RB - 1) / RB);
+          kern<<<(unsigned)(p->m * nblk), 256, sm, st>>>(d, mat, io, li.max_in, li.max_out, li.max_rows, li.max_cols,
+                                                          nblk);
+          IDBF_CUDA_TRY(cudaGetLastError());
+          continue;
+        }
+      }
       const size_t sm = (size_t)RB * (li.max_out * sizeof(V) + 2 * gcap * sizeof(typename P::gv_t) +
                                       2 * rcap * sizeof(V) + li.max_in * sizeof(V));
       if (sm > 200 * 1024) return IDBF_EUNSUPPORTED;
@@ -814,8 +840,8 @@ static idbf_status apply_common(idbf_plan h, const void* x, void* y, int64_t nrh
   cudaStream_t st = (cudaStream_t)stream;
   if (mode == IDBF_MODE_TF32X3) return apply_tf32x3(p, x, y, nrhs, ld, st);
   const bool one = nrhs == 1;
-  // forward with several right-hand sides in FP32 / FP64: 16 per tile from 16 on, else 8
-  const bool wide = !adjoint && nrhs >= 16, mid = !adjoint && nrhs > 1;
+  // several right-hand sides in FP32 / FP64 (forward and adjoint): 16 per tile from 16 on, else 8
+  const bool wide = nrhs >= 16, mid = nrhs > 1;
   idbf_status s2 = IDBF_EUNSUPPORTED;
   switch (mode) {
     case IDBF_MODE_FP64:

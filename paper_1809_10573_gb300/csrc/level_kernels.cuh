@@ -867,4 +867,237 @@ __device__ __forceinline__ void fwd_node_warp(const DevLevel& d, const typename 
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Tiled adjoint node for several right-hand sides (FP32 and FP64 policies). The adjoint of a
+// block product y_c = M_c g_c is res_c = M_c^* y_c: a reduction over the block's rows whose
+// outputs are its columns. One CTA computes node j for right-hand sides r0 .. r0+nrb-1:
+//   - the adjoint inputs v (the forward outputs of the node) are staged once, with, per block,
+//     the element of v that each block row multiplies (gsrc) and the block's index lists;
+//   - chunks of KR whole rows of a block (all its columns; in a column-major block a row chunk is
+//     one short piece per column) flow through a ring of STAGES stages filled with cp.async and
+//     laid out row-major with a padded row stride, so a thread's TI consecutive columns are one
+//     vector load and a warp's stores and loads spread over the banks;
+//   - every thread keeps a TI x TC tile (columns x right-hand sides) in registers over all the
+//     chunks; blocks with few column tiles split their rows over S = 2 .. 16 neighbouring lanes,
+//     combined by warp shuffles once per block;
+//   - outputs are the forward inputs of the node. U level: segment c gets v[q_c] + res_c (each
+//     block its own segment). S level: res_0 + res_1 over the same columns. V level: every input
+//     element receives one term from each block (v_c[r] at q_c[r] and res_c[i] at p_c[i]). Where
+//     two blocks meet, block 0 stores and block 1 adds after a barrier (two terms: the order of
+//     the addition cannot change the sum).
+namespace tadj {
+constexpr int TI = 8, TC = 4, KR = 8, STAGES = 2;
+// row stride of a staged chunk: even (16-byte aligned vectors of two complex64 columns) and
+// = 2 mod 16 columns, so that the rows of a chunk start in different banks
+__host__ __device__ constexpr int col_pad(int cols) {
+  return (cols + 15) / 16 * 16 + 2;  // >= the last column tile's end (TI = 8 divides 16)
+}
+template <class P>
+__host__ __device__ constexpr size_t stage_bytes(int max_cols) {
+  return ((size_t)KR * col_pad(max_cols) * sizeof(typename P::mat_t) + 15) & ~(size_t)15;
+}
+// shared memory: v[max_out][RB] | ring | gsrc[2][max_rows] | lists[2][icap]
+template <class P, int RB>
+__host__ __device__ constexpr size_t smem_bytes(int max_in, int max_out, int max_rows, int max_cols) {
+  return (((size_t)max_out * RB * sizeof(typename P::vec_t) + 15) & ~(size_t)15) + STAGES * stage_bytes<P>(max_cols) +
+         2 * (size_t)(max_rows + 4) * sizeof(int32_t) +
+         2 * (size_t)((max_in > max_out ? max_in : max_out) + 4) * sizeof(int32_t);
+}
+template <int ES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src),
+               "n"(ES)
+               : "memory");
+}
+// TI consecutive staged entries (16-byte aligned)
+template <class P>
+__device__ __forceinline__ void load_cols(const typename P::mat_t* p, typename P::mat_t (&m)[TI]) {
+  if constexpr (sizeof(typename P::mat_t) == 8) {
+#pragma unroll
+    for (int c = 0; c < TI; c += 2) {
+      const float4 v = *reinterpret_cast<const float4*>(p + c);
+      m[c] = make_float2(v.x, v.y);
+      m[c + 1] = make_float2(v.z, v.w);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < TI; ++c) m[c] = p[c];
+  }
+}
+}  // namespace tadj
+
+template <class P, int RB>
+__device__ __forceinline__ void adj_node_tiled(const DevLevel& d, const typename P::mat_t* __restrict__ mat,
+                                               const IO<typename P::vec_t>& io, int max_in, int max_out,
+                                               int max_rows, int max_cols, int64_t j, int r0, unsigned char* smem) {
+  using namespace tadj;
+  using V = typename P::vec_t;
+  using G = typename P::gv_t;
+  using M = typename P::mat_t;
+  using A = typename P::acc_t;
+  static_assert(std::is_same<V, G>::value, "operands used as stored (FP32 and FP64 policies)");
+  static_assert(RB % TC == 0 && (RB * sizeof(V)) % 16 == 0, "16-byte aligned operand rows");
+  constexpr int ES = (int)sizeof(M);
+  constexpr int TCN = TC;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nrb = min(RB, io.R - r0);
+  V* v = (V*)smem;
+  unsigned char* ring = smem + (((size_t)max_out * RB * sizeof(V) + 15) & ~(size_t)15);
+  const size_t sbytes = stage_bytes<P>(max_cols);
+  int32_t* gsrc = (int32_t*)(ring + STAGES * sbytes);
+  int32_t* lists = gsrc + 2 * (max_rows + 4);
+  const int icap = (max_in > max_out ? max_in : max_out) + 4;
+
+  // adjoint inputs (the forward outputs of node j) -> v
+  int o0len, o1len;
+  if (d.lev == d.L) {
+    o0len = d.n0;
+    o1len = 0;
+    for (int i = tid; i < o0len * RB; i += nt) {
+      const int rb = i / o0len, e = i - rb * o0len;
+      v[e * RB + rb] = rb < nrb ? io.x[j * d.n0 + e + (int64_t)(r0 + rb) * io.ldx] : P::zero();
+    }
+  } else {
+    const int64_t s0 = out_seg_id(d, j, 0), s1 = out_seg_id(d, j, 1);
+    o0len = d.out_len[s0];
+    o1len = d.out_len[s1];
+    const int64_t b0 = d.out_off[s0], b1 = d.out_off[s1];
+    for (int i = tid; i < (o0len + o1len) * RB; i += nt) {
+      const int e = i / RB, rb = i % RB;
+      const int64_t off = e < o0len ? b0 + e : b1 + (e - o0len);
+      v[i] = rb < nrb ? io.win[off * io.R + r0 + rb] : P::zero();
+    }
+  }
+  const int rowsv[2] = {d.rows[2 * j], d.rows[2 * j + 1]};
+  const int colsv[2] = {d.cols[2 * j], d.cols[2 * j + 1]};
+  const int64_t mov[2] = {d.moff[2 * j], d.moff[2 * j + 1]};
+  // block lists and the element of v each block row multiplies
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int32_t* ix = d.idx + d.ioff[2 * j + c];
+    const int nl = d.kind == KIND_S ? 0 : rowsv[c] + colsv[c];
+    for (int i = tid; i < nl; i += nt) lists[c * icap + i] = ix[i];
+    for (int r = tid; r < rowsv[c]; r += nt)
+      gsrc[c * (max_rows + 4) + r] = d.kind == KIND_U ? ix[colsv[c] + r] : (c ? o0len : 0) + r;
+  }
+  // forward input element e of the node (the adjoint's output), right-hand side rb
+  int len0 = 0;
+  int64_t ib0 = 0, ib1 = 0;
+  if (d.lev > 0) {
+    len0 = d.in_len[2 * j];
+    ib0 = d.in_off[2 * j];
+    ib1 = d.in_off[2 * j + 1];
+  }
+  auto in_ptr = [&](int e, int rb) -> V* {
+    if (d.lev == 0) return io.y + j * d.n0 + e + (int64_t)(r0 + rb) * io.ldy;
+    return io.wout + (e < len0 ? ib0 + e : ib1 + (e - len0)) * io.R + r0 + rb;
+  };
+  __syncthreads();
+  const int nct = (nrb + TCN - 1) / TCN;
+  for (int c = 0; c < 2; ++c) {
+    const int rows = rowsv[c], cols = colsv[c];
+    const int32_t* lst = lists + c * icap;
+    const int32_t* gs = gsrc + c * (max_rows + 4);
+    const M* Mc = mat + mov[c];
+    const int cp = col_pad(cols);
+    const bool add = c == 1 && d.kind != KIND_U;  // second term of an S or V output
+    if (add) __syncthreads();                      // block 0's terms are in place
+    if (d.kind == KIND_V) {  // pass-through: v_c[r] -> input element q_c[r]
+      for (int i = tid; i < rows * nrb; i += nt) {
+        const int r = i / nrb, rb = i - r * nrb;
+        V* dst = in_ptr(lst[r], rb);
+        const V val = v[(size_t)((c ? o0len : 0) + r) * RB + rb];
+        *dst = add ? P::add(*dst, val) : val;
+      }
+    }
+    const int nit = (cols + TI - 1) / TI;
+    const int tasks = nit * nct;
+    if (tasks == 0) continue;
+    int S = 1;
+    while (S < 16 && 2 * S * tasks <= nt) S *= 2;
+    const int rounds = S > 1 ? 1 : (tasks + nt - 1) / nt;
+    const int nch = rows > 0 ? (rows + KR - 1) / KR : 0;
+    // rows q*KR .. of the block, all columns, into stage q % STAGES (row-major, stride cp)
+    auto issue = [&](int q) {
+      const int kr = min(KR, rows - q * KR);
+      unsigned char* st = ring + (size_t)(q % STAGES) * sbytes;
+      for (int e = tid; e < kr * cols; e += nt) {
+        const int col = e / kr, r = e - col * kr;
+        cp_async_elem<ES>(st + ((size_t)r * cp + col) * ES, Mc + (int64_t)col * rows + q * KR + r);
+      }
+    };
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int w = S > 1 ? tid / S : rd * nt + tid;
+      const int sl = S > 1 ? tid - w * S : 0;
+      const bool active = w < tasks;
+      const int it = active ? w % nit : 0;
+      const int ct = active ? w / nit : 0;
+      A acc[TI][TCN];
+#pragma unroll
+      for (int ti = 0; ti < TI; ++ti)
+#pragma unroll
+        for (int cc = 0; cc < TCN; ++cc) P::init(acc[ti][cc]);
+#pragma unroll
+      for (int q = 0; q < STAGES - 1; ++q) {
+        if (q < nch) issue(q);
+        tiled::cp_async_commit();
+      }
+      for (int q = 0; q < nch; ++q) {
+        tiled::cp_async_wait<STAGES - 2>();
+        __syncthreads();  // chunk q landed for every thread; the stage of chunk q-1 is free again
+        if (q + STAGES - 1 < nch) issue(q + STAGES - 1);
+        tiled::cp_async_commit();
+        if (active) {
+          const int kr = min(KR, rows - q * KR);
+          const M* st = (const M*)(ring + (size_t)(q % STAGES) * sbytes);
+          for (int r = sl; r < kr; r += S) {
+            G b[TCN];
+            tiled::load_ops<P, TCN>(v + (size_t)gs[q * KR + r] * RB + ct * TCN, b);
+            M m[TI];
+            load_cols<P>(st + (size_t)r * cp + it * TI, m);
+#pragma unroll
+            for (int ti = 0; ti < TI; ++ti)
+#pragma unroll
+              for (int cc = 0; cc < TCN; ++cc) P::macc(acc[ti][cc], m[ti], b[cc]);
+          }
+        }
+      }
+      __syncthreads();  // the ring is free for the next pass
+      // the S row slices of a task are neighbouring lanes
+      for (int o = 1; o < S; o <<= 1) {
+#pragma unroll
+        for (int ti = 0; ti < TI; ++ti)
+#pragma unroll
+          for (int cc = 0; cc < TCN; ++cc) {
+            acc[ti][cc].re += __shfl_xor_sync(0xffffffffu, acc[ti][cc].re, o);
+            acc[ti][cc].im += __shfl_xor_sync(0xffffffffu, acc[ti][cc].im, o);
+          }
+      }
+      if (active && sl == 0) {
+#pragma unroll
+        for (int ti = 0; ti < TI; ++ti) {
+          const int i = it * TI + ti;
+          if (i >= cols) continue;
+#pragma unroll
+          for (int cc = 0; cc < TCN; ++cc) {
+            const int rb = ct * TCN + cc;
+            if (rb >= nrb) continue;
+            V val = P::fin(acc[ti][cc]);
+            V* dst;
+            if (d.kind == KIND_U) {  // forward input segment c: v[q_c[i]] + res_c[i]
+              val = P::add(val, v[(size_t)lst[i] * RB + rb]);
+              dst = in_ptr((c ? colsv[0] : 0) + i, rb);
+            } else {
+              dst = in_ptr(d.kind == KIND_S ? i : lst[rows + i], rb);
+              if (add) val = P::add(*dst, val);
+            }
+            *dst = val;
+          }
+        }
+      }
+    }
+  }
+  tiled::cp_async_wait<0>();
+}
+
 }  // namespace idbf

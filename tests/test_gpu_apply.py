@@ -68,15 +68,20 @@ def test_fp32_apply_matches_oracle_to_single_precision(case):
 @pytest.mark.parametrize("case", ["fio_base_4096", "dft_jit_2048_oddL", "fio_paper_2048"])
 @pytest.mark.parametrize("nrhs", [2, 16, 19])
 def test_multi_rhs_register_tiles_match_oracle(case, nrhs):
-    """FP64 and FP32 forward applies with several right-hand sides run the register-tiled level
-    kernel (8 right-hand sides per CTA below 16, 16 from 16 on; 19 leaves a ragged last block)."""
+    """FP64 and FP32 forward and adjoint applies with several right-hand sides run the
+    register-tiled level kernels (8 right-hand sides per CTA below 16, 16 from 16 on; 19 leaves a
+    ragged last block)."""
     c, plan = _plan(case)
     plan.set_storage(P.STORE_C128, P.STORE_C64)
     X = inputs.complex_gaussian(c["N"], nrhs, seed=16)
     ref = idbf.apply(c["F"], X)
-    assert rel(plan.apply(torch.from_numpy(X).cuda(), mode=P.MODE_FP64).cpu().numpy(), ref) < 1e-12
+    ref_a = idbf.apply_adjoint(c["F"], X)
+    x64 = torch.from_numpy(X).cuda()
+    assert rel(plan.apply(x64, mode=P.MODE_FP64).cpu().numpy(), ref) < 1e-12
+    assert rel(plan.apply_adjoint(x64, mode=P.MODE_FP64).cpu().numpy(), ref_a) < 1e-12
     x32 = torch.from_numpy(X.astype(np.complex64)).cuda()
     assert rel(plan.apply(x32, mode=P.MODE_FP32).cpu().numpy(), ref) < 2e-5
+    assert rel(plan.apply_adjoint(x32, mode=P.MODE_FP32).cpu().numpy(), ref_a) < 2e-5
 
 
 def test_leading_dimension_and_preallocated_output():
