@@ -358,7 +358,29 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     if (lane != 0) return;
     uint32_t it = 0, nn = 0;
     bool ok = true;
+    // node descriptions are loaded one node ahead, so that no copy waits for them
+    struct Meta {
+      int64_t in0, io[2], mo[2];
+      int l0, l1, rows[2], cols[2];
+    };
+    auto meta = [&](int64_t jj) {
+      Meta m;
+      m.in0 = d.lev == 0 ? 0 : d.in_off[2 * jj];
+      m.l0 = d.lev == 0 ? d.n0 : d.in_len[2 * jj];
+      m.l1 = d.lev == 0 ? 0 : d.in_len[2 * jj + 1];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        m.io[c] = d.ioff[2 * jj + c];
+        m.mo[c] = d.moff[2 * jj + c];
+        m.rows[c] = d.rows[2 * jj + c];
+        m.cols[c] = d.cols[2 * jj + c];
+      }
+      return m;
+    };
+    Meta nxt = meta(blockIdx.x < d.m ? (int64_t)blockIdx.x : 0);
     for (int64_t j = blockIdx.x; j < d.m && ok; j += gridDim.x, ++nn) {
+      const Meta cur = nxt;
+      if (j + gridDim.x < d.m) nxt = meta(j + gridDim.x);
       // node inputs and index lists into buffer nn & 1 (released by the consumers of node nn-2)
       const int b = nn & 1;
       if (!wait_bounded(&in_empty[b], ((nn >> 1) & 1) ^ 1, limit_ns, &abort_flag)) { ok = false; break; }
@@ -368,8 +390,8 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
         usrc = (const unsigned char*)(io.x + j * d.n0);
         ubytes = inputs_bulk ? (uint32_t)(d.n0 * VS) : 0;
       } else {
-        usrc = (const unsigned char*)(io.win + d.in_off[2 * j]);
-        ubytes = inputs_bulk ? (uint32_t)((d.in_len[2 * j] + d.in_len[2 * j + 1]) * VS) : 0;
+        usrc = (const unsigned char*)(io.win + cur.in0);
+        ubytes = inputs_bulk ? (uint32_t)((cur.l0 + cur.l1) * VS) : 0;
       }
       const unsigned char* ua = (const unsigned char*)((uintptr_t)usrc & ~(uintptr_t)15);
       const uint32_t ucopy = ubytes ? (uint32_t)((((uintptr_t)usrc + ubytes + 15) & ~(uintptr_t)15) - (uintptr_t)ua) : 0;
@@ -377,8 +399,8 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       const unsigned char* ia[2] = {nullptr, nullptr};
       if (d.kind != KIND_S && inputs_bulk) {
         for (int c = 0; c < 2; ++c) {
-          const unsigned char* is = (const unsigned char*)(d.idx + d.ioff[2 * j + c]);
-          const uint32_t ib = (uint32_t)((d.rows[2 * j + c] + d.cols[2 * j + c]) * 4);
+          const unsigned char* is = (const unsigned char*)(d.idx + cur.io[c]);
+          const uint32_t ib = (uint32_t)((cur.rows[c] + cur.cols[c]) * 4);
           ia[c] = (const unsigned char*)((uintptr_t)is & ~(uintptr_t)15);
           icopy[c] = (uint32_t)((((uintptr_t)is + ib + 15) & ~(uintptr_t)15) - (uintptr_t)ia[c]);
         }
@@ -392,10 +414,10 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       }
       // the blocks, a few whole columns per stage
       for (int c = 0; c < 2 && ok; ++c) {
-        const int rows = d.rows[2 * j + c], cols = d.cols[2 * j + c];
+        const int rows = cur.rows[c], cols = cur.cols[c];
         if (rows == 0 || cols == 0) continue;
         const int cpc = cols_per_chunk(rows, ES, STAGE_BYTES);
-        const unsigned char* base = (const unsigned char*)(mat + d.moff[2 * j + c]);
+        const unsigned char* base = (const unsigned char*)(mat + cur.mo[c]);
         for (int j0 = 0; j0 < cols; j0 += cpc, ++it) {
           const int nc = min(cpc, cols - j0);
           const int stg = it % STAGES;
@@ -442,11 +464,24 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     else { l0 = d.in_len[2 * j]; l1 = d.in_len[2 * j + 1]; }
     const int rows0 = d.rows[2 * j], rows1 = d.rows[2 * j + 1];
     const int cols0 = d.cols[2 * j], cols1 = d.cols[2 * j + 1];
+    // where the node's outputs go, loaded now so that the epilogues after the barriers below do
+    // not wait for them
+    int64_t obv[2] = {0, 0};
+    int olen0 = 0;
+    const int64_t in0 = d.lev == 0 ? 0 : d.in_off[2 * j];
+    const int64_t iov[2] = {d.kind != KIND_S ? d.ioff[2 * j] : 0, d.kind != KIND_S ? d.ioff[2 * j + 1] : 0};
+    const int64_t mov[2] = {d.moff[2 * j], d.moff[2 * j + 1]};
+    if (d.lev < d.L) {
+      const int64_t s0 = out_seg_id(d, j, 0), s1 = out_seg_id(d, j, 1);
+      obv[0] = d.out_off[s0];
+      obv[1] = d.out_off[s1];
+      olen0 = d.out_len[s0];
+    }
     if (!failed && !wait_bounded(&in_full[b], (nn >> 1) & 1, limit_ns, &abort_flag)) failed = true;
     // inputs (shifted within 16 bytes of the copy) and index lists in shared memory
     const V* u;
     {
-      const uintptr_t usrc = d.lev == 0 ? (uintptr_t)(io.x + j * d.n0) : (uintptr_t)(io.win + d.in_off[2 * j]);
+      const uintptr_t usrc = d.lev == 0 ? (uintptr_t)(io.x + j * d.n0) : (uintptr_t)(io.win + in0);
       u = ubuf + (size_t)b * geo.ucap + (int)((usrc & 15) / VS);
     }
     if (!inputs_bulk) {  // plain loads by the consumers
@@ -454,7 +489,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       if (d.lev == 0) {
         for (int i = tc; i < l0; i += NCT) uw[i] = io.x[j * d.n0 + i];
       } else {
-        const V* src = io.win + d.in_off[2 * j];
+        const V* src = io.win + in0;
         for (int i = tc; i < l0 + l1; i += NCT) uw[i] = src[i];
       }
       u = uw;
@@ -464,13 +499,13 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     if (d.kind != KIND_S) {
       int32_t* ib0 = ibuf + (size_t)b * geo.icap;
       if (inputs_bulk) {
-        const uintptr_t s0 = (uintptr_t)(d.idx + d.ioff[2 * j]), s1 = (uintptr_t)(d.idx + d.ioff[2 * j + 1]);
+        const uintptr_t s0 = (uintptr_t)(d.idx + iov[0]), s1 = (uintptr_t)(d.idx + iov[1]);
         const uint32_t c0 = (uint32_t)((((s0 + (rows0 + cols0) * 4 + 15) & ~(uintptr_t)15)) - (s0 & ~(uintptr_t)15));
         ix0 = ib0 + (int)((s0 & 15) / 4);
         ix1 = ib0 + ((c0 / 4 + 3) & ~3) + (int)((s1 & 15) / 4);
       } else {
-        const int32_t* g0 = d.idx + d.ioff[2 * j];
-        const int32_t* g1 = d.idx + d.ioff[2 * j + 1];
+        const int32_t* g0 = d.idx + iov[0];
+        const int32_t* g1 = d.idx + iov[1];
         for (int i = tc; i < rows0 + cols0; i += NCT) ib0[i] = g0[i];
         for (int i = tc; i < rows1 + cols1; i += NCT) ib0[rows0 + cols0 + i] = g1[i];
         ix0 = ib0;
@@ -504,7 +539,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       const bool work = rows > 0 && cols > 0;
       if (work) {
         const int cpc = cols_per_chunk(rows, ES, STAGE_BYTES);
-        const uintptr_t base = (uintptr_t)(mat + d.moff[2 * j + c]);
+        const uintptr_t base = (uintptr_t)(mat + mov[c]);
         const uint32_t chunk_bytes = (uint32_t)cpc * rows * ES;
         int since = 0;
         uintptr_t src = base;
@@ -551,7 +586,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       }
       consumer_sync<NCT>();
       // no early exit here: every consumer warp must reach the barriers of this block
-      const int64_t s_out = d.lev < d.L ? out_seg_id(d, j, c) : 0;
+      const int64_t ob = obv[c];
       if (work && team == 0 && !failed) {
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
@@ -563,12 +598,12 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
             V* q = &t[ix[(c ? l1 : l0) + r]];
             *q = c ? P::add(*q, v) : v;
           } else {
-            io.wout[d.out_off[s_out] + r] = d.kind == KIND_V ? P::add(v, u[ix[r]]) : v;
+            io.wout[ob + r] = d.kind == KIND_V ? P::add(v, u[ix[r]]) : v;
           }
         }
       }
       if (d.kind == KIND_V && cols == 0 && !failed) {  // all skeleton: out = u[q]
-        for (int r = tc; r < rows; r += NCT) io.wout[d.out_off[s_out] + r] = u[ix[r]];
+        for (int r = tc; r < rows; r += NCT) io.wout[ob + r] = u[ix[r]];
       }
       consumer_sync<NCT>();  // red is reused by the next block; t must be complete before c = 1
     }
@@ -585,10 +620,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       if (d.lev == d.L) {
         for (int i = tc; i < tl; i += NCT) io.y[j * d.n0 + i] = t[i];
       } else {
-        const int64_t s0 = out_seg_id(d, j, 0), s1 = out_seg_id(d, j, 1);
-        const int len0 = d.out_len[s0];
-        const int64_t b0 = d.out_off[s0], b1 = d.out_off[s1];
-        for (int i = tc; i < tl; i += NCT) io.wout[i < len0 ? b0 + i : b1 + (i - len0)] = t[i];
+        for (int i = tc; i < tl; i += NCT) io.wout[i < olen0 ? obv[0] + i : obv[1] + (i - olen0)] = t[i];
       }
     }
   }
