@@ -791,35 +791,49 @@ __device__ __forceinline__ void fwd_node_warp(const DevLevel& d, const typename 
     const int rows = rowsv[c], cols = colsv[c];
     const M* Mc = mat + mov[c];
     const G* gc = g + (d.kind == KIND_S ? 0 : c * gcap);
-    typename P::acc_t acc[RPL];
+    // two accumulators per row (even and odd columns): two independent dependency chains
+    typename P::acc_t acc0[RPL], acc1[RPL];
 #pragma unroll
-    for (int i = 0; i < RPL; ++i) P::init(acc[i]);
-    int k = 0;
-    for (; k + P::CHUNK <= cols; k += P::CHUNK) {
-#pragma unroll 8
-      for (int q = 0; q < P::CHUNK; ++q) {
-        const G gv = gc[k + q];
-#pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-          const int r = lane + 32 * i;
-          if (r < rows) P::mac(acc[i], P::ld(Mc + (int64_t)(k + q) * rows + r), gv);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < RPL; ++i) P::flush(acc[i]);
+    for (int i = 0; i < RPL; ++i) {
+      P::init(acc0[i]);
+      P::init(acc1[i]);
     }
-    for (; k < cols; ++k) {
-      const G gv = gc[k];
+    auto pair = [&](int kk) {  // columns kk (into acc0) and kk + 1 (into acc1)
+      const G g0 = gc[kk], g1 = gc[kk + 1];
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
         const int r = lane + 32 * i;
-        if (r < rows) P::mac(acc[i], P::ld(Mc + (int64_t)k * rows + r), gv);
+        if (r < rows) {
+          P::mac(acc0[i], P::ld(Mc + (int64_t)kk * rows + r), g0);
+          P::mac(acc1[i], P::ld(Mc + (int64_t)(kk + 1) * rows + r), g1);
+        }
+      }
+    };
+    int k = 0;
+    for (; k + 2 * P::CHUNK <= cols; k += 2 * P::CHUNK) {
+#pragma unroll 4
+      for (int q = 0; q < 2 * P::CHUNK; q += 2) pair(k + q);
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        P::flush(acc0[i]);
+        P::flush(acc1[i]);
+      }
+    }
+    for (; k + 1 < cols; k += 2) pair(k);
+    if (k < cols) {
+      const G g0 = gc[k];
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        if (r < rows) P::mac(acc0[i], P::ld(Mc + (int64_t)k * rows + r), g0);
       }
     }
 #pragma unroll
     for (int i = 0; i < RPL; ++i) {
-      P::flush(acc[i]);
-      res[c][i] = P::fin(acc[i]);
+      P::flush(acc0[i]);
+      P::flush(acc1[i]);
+      P::combine(acc0[i], P::part(acc1[i]));
+      res[c][i] = P::fin(acc0[i]);
     }
     if (d.kind != KIND_U) {
       const int64_t ob = d.out_off[out_seg_id(d, j, c)];
