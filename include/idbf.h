@@ -65,9 +65,13 @@ typedef enum {
  *   c_profile 0: c(x) = (2 + sin(2 pi x) sin(4 pi x)) / 3
  *   c_profile 1: c(x) = (2 + 0.2 sin(2 pi x)) / 16   (Example 1 as printed)
  *   c_profile 2: c(x) = 0
- * IDBF_KERNEL_DFT:   K(x, xi) = exp(sign 2 pi i x xi), sign = +1 or -1   (Example 3) */
+ * IDBF_KERNEL_DFT:   K(x, xi) = exp(sign 2 pi i x xi), sign = +1 or -1   (Example 3)
+ * IDBF_KERNEL_J0:    K(x, xi) = J_0(x xi), the Schloemilch expansion of Example 2 (Eq. S) on
+ *                    x_k = (k-1)/N, xi_n = n pi; a real kernel (zero imaginary parts); J_0 is
+ *                    CUDA's j0; sign and c_profile are ignored */
 #define IDBF_KERNEL_FIO1D 0
 #define IDBF_KERNEL_DFT 1
+#define IDBF_KERNEL_J0 2
 typedef struct {
   int32_t kind;
   int32_t sign;

@@ -4,6 +4,8 @@ Example 1 (1D FIO):  K(x, xi) = exp(2 pi i Phi(x, xi)),  Phi = x xi + c(x) |xi|.
   c profile 0: c(x) = (2 + sin(2 pi x) sin(4 pi x)) / 3   (the large-c' variant benchmarked here)
   c profile 1: c(x) = (2 + 0.2 sin(2 pi x)) / 16           (the profile printed in Example 1)
   c profile 2: c(x) = 0                                    (reduces K to an inverse DFT)
+Example 2 (Schloemilch expansion, Eq. S): K(x, xi) = J_0(x xi), with x_k = (k-1)/N and
+  xi_n = n pi; J_0 from scipy.special (a library step), a real kernel held as complex128.
 Example 3 (DFT type): K(x, xi) = exp(sign * 2 pi i x xi), sign = -1 by default.
 
 Each entry is sampled individually in O(1) (the premise of Sec. 1). The phase is reduced
@@ -18,6 +20,7 @@ import numpy as np
 
 KIND_FIO = 0
 KIND_DFT = 1
+KIND_J0 = 2
 
 _SPLIT = 134217729.0  # 2^27 + 1, Veltkamp splitting constant for binary64
 
@@ -72,6 +75,11 @@ class Kernel:
 
     def entries(self, x, xi, rows, cols):
         """The block K(x[rows], xi[cols]) as a dense complex128 matrix."""
+        if self.kind == KIND_J0:
+            from scipy.special import j0
+            X = np.asarray(x, dtype=np.float64)[np.asarray(rows)][:, None]
+            XI = np.asarray(xi, dtype=np.float64)[np.asarray(cols)][None, :]
+            return j0(X * XI).astype(np.complex128)
         ph = self.phase(x[np.asarray(rows)], xi[np.asarray(cols)])
         return np.exp(2j * np.pi * ph)
 

@@ -13,11 +13,11 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (KERNEL_DFT, KERNEL_FIO1D, MODE_DF64, MODE_FP32, MODE_FP64, MODE_TF32X3,
+from ._lib import (KERNEL_DFT, KERNEL_FIO1D, KERNEL_J0, MODE_DF64, MODE_FP32, MODE_FP64, MODE_TF32X3,
                    SAMPLE_ALL, SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, STORE_C64, STORE_C128,
                    STORE_DF64, IDBFError)
 
-__all__ = ["Plan", "Batch", "IDBFError", "apply", "IDBFApply", "kernel_matvec_rows", "KERNEL_FIO1D", "KERNEL_DFT", "MODE_FP64",
+__all__ = ["Plan", "Batch", "IDBFError", "apply", "IDBFApply", "kernel_matvec_rows", "KERNEL_FIO1D", "KERNEL_DFT", "KERNEL_J0", "MODE_FP64",
            "MODE_DF64", "MODE_FP32", "MODE_TF32X3", "STORE_C128", "STORE_DF64", "STORE_C64",
            "SAMPLE_MOCK_CHEBYSHEV", "SAMPLE_RANDOM", "SAMPLE_ALL"]
 
@@ -58,7 +58,7 @@ class Plan:
               oversample=1.0, oversample_leaf=0.0, sampling=SAMPLE_MOCK_CHEBYSHEV, seed=0,
               storage=STORE_C128, stream=None):
         L = _lib.lib()
-        k = _lib.Kernel(KERNEL_FIO1D if kernel == "fio" else KERNEL_DFT, sign, c_profile, 0)
+        k = _lib.Kernel(_kernel_kind(kernel), sign, c_profile, 0)
         p = _lib.Params()
         L.idbf_default_params(C.byref(p))
         p.eps, p.leaf, p.rank_cap, p.oversample, p.oversample_leaf = eps, leaf, rank_cap, oversample, oversample_leaf
@@ -259,10 +259,18 @@ class Batch:
             pass
 
 
+def _kernel_kind(name: str) -> int:
+    """"fio" (Example 1), "dft" (Example 3) or "j0" (Example 2, the Schloemilch expansion)."""
+    kinds = {"fio": KERNEL_FIO1D, "dft": KERNEL_DFT, "j0": KERNEL_J0}
+    if name not in kinds:
+        raise ValueError(f"unknown kernel {name!r}: one of {sorted(kinds)}")
+    return kinds[name]
+
+
 def kernel_matvec_rows(x, xi, v, rows, kernel="fio", c_profile=0, sign=-1, stream=None):
     """Direct (dense) rows of K v on the GPU: the ground truth u^d of Sec. 3 at `rows`.
     x, xi: float64 CUDA tensors; v: complex128 CUDA tensor (N,); rows: int64 CUDA tensor."""
-    k = _lib.Kernel(KERNEL_FIO1D if kernel == "fio" else KERNEL_DFT, sign, c_profile, 0)
+    k = _lib.Kernel(_kernel_kind(kernel), sign, c_profile, 0)
     y = torch.empty(rows.numel(), dtype=torch.complex128, device=v.device)
     for t, dt in ((x, torch.float64), (xi, torch.float64), (v, torch.complex128), (rows, torch.int64)):
         if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libidbf.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ERANKCAP, ETIMEOUT, EFORMAT, EUNSUPPORTED = range(8)
-KERNEL_FIO1D, KERNEL_DFT = 0, 1
+KERNEL_FIO1D, KERNEL_DFT, KERNEL_J0 = 0, 1, 2
 SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, SAMPLE_ALL = 0, 1, 2
 STORE_C128, STORE_DF64, STORE_C64 = 0, 1, 2
 MODE_FP64, MODE_DF64, MODE_FP32, MODE_TF32X3 = 0, 1, 2, 3

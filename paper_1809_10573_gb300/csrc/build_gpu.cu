@@ -58,6 +58,7 @@ __global__ void k_cprofile(const double* __restrict__ x, double* __restrict__ cx
 }
 
 __device__ __forceinline__ double2 kentry(const KDesc& K, double x, double cx, double xi) {
+  if (K.kind == IDBF_KERNEL_J0) return make_double2(j0(x * xi), 0.0);  // Example 2
   double ph;
   if (K.kind == IDBF_KERNEL_FIO1D) ph = frac_prod(x, xi) + frac_prod(cx, fabs(xi));
   else ph = (double)K.sign * frac_prod(x, xi);
@@ -933,7 +934,8 @@ extern "C" idbf_status idbf_kernel_matvec_rows(const idbf_kernel* kernel, const 
                                                const int64_t* rows, int64_t nrows, const void* v, void* y,
                                                void* stream) {
   if (!kernel || !x || !xi || !rows || !v || !y || N < 1 || nrows < 0 || nrows > (1LL << 31) - 1) return IDBF_EINVAL;
-  if (kernel->kind != IDBF_KERNEL_FIO1D && kernel->kind != IDBF_KERNEL_DFT) return IDBF_EINVAL;
+  if (kernel->kind != IDBF_KERNEL_FIO1D && kernel->kind != IDBF_KERNEL_DFT && kernel->kind != IDBF_KERNEL_J0)
+    return IDBF_EINVAL;
   if (nrows == 0) return IDBF_OK;
   bld::KDesc K{kernel->kind, kernel->sign, kernel->c_profile};
   bld::k_dense_rows<<<(unsigned)nrows, 256, 0, (cudaStream_t)stream>>>(K, x, xi, N, rows, (const double2*)v, (double2*)y);
@@ -958,7 +960,7 @@ extern "C" idbf_status idbf_build(const idbf_kernel* kernel, const double* x_hos
     if (kernel->c_profile < 0 || kernel->c_profile > 2) return IDBF_EINVAL;
   } else if (kernel->kind == IDBF_KERNEL_DFT) {
     if (kernel->sign != 1 && kernel->sign != -1) return IDBF_EINVAL;
-  } else {
+  } else if (kernel->kind != IDBF_KERNEL_J0) {
     return IDBF_EINVAL;
   }
   for (int64_t i = 1; i < N; ++i)

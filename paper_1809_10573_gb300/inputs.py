@@ -22,6 +22,12 @@ def uniform_grid(N: int):
     return i / N, i - N / 2
 
 
+def schlomilch_grid(N: int):
+    """Example 2 grid: x_k = (k-1)/N (k = 1..N) and xi_n = n pi (n = 1..N)."""
+    i = np.arange(N, dtype=np.float64)
+    return i / N, (i + 1.0) * np.pi
+
+
 def jittered_grid(N: int, seed: int, jitter: float = 0.3):
     """x_i = i/N + U(-jitter, jitter)/N, xi_j = j - N/2 (sorted: |jitter| < 1/2)."""
     rng = np.random.default_rng(seed)

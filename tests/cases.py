@@ -14,16 +14,23 @@ CASES = {
     "fio_base_4096": (4096, 64, ("fio", 0, 0), "uniform", 1e-8, dict(t=2, t_leaf=4)),  # config 1
     "fio_paper_2048": (2048, 8, ("fio", 0, 1), "uniform", 1e-6, {}),                # Example 1, L = 8
     "fio_base_8192_oddL": (8192, 64, ("fio", 0, 0), "uniform", 1e-6, dict(t=2, t_leaf=4)),  # L = 7
+    "j0_2048": (2048, 16, ("j0", 0, 0), "schlomilch", 1e-8, dict(t=2, t_leaf=4)),   # Example 2, L = 7
 }
 
 
 def kernel_of(spec):
     kind, sign, prof = spec
-    return kernels.Kernel(kernels.KIND_FIO if kind == "fio" else kernels.KIND_DFT, sign=sign, c_profile=prof)
+    kinds = {"fio": kernels.KIND_FIO, "dft": kernels.KIND_DFT, "j0": kernels.KIND_J0}
+    return kernels.Kernel(kinds[kind], sign=sign, c_profile=prof)
 
 
 def grid_of(name, N):
-    return inputs.uniform_grid(N) if CASES[name][3] == "uniform" else inputs.jittered_grid(N, seed=N)
+    grid = CASES[name][3]
+    if grid == "uniform":
+        return inputs.uniform_grid(N)
+    if grid == "schlomilch":
+        return inputs.schlomilch_grid(N)
+    return inputs.jittered_grid(N, seed=N)
 
 
 @functools.lru_cache(maxsize=None)

@@ -51,11 +51,14 @@ def test_exact_mode_dft():
     (4096, 64, 1e-8, "uniform", "fio", 0, dict(oversample=2.0, oversample_leaf=4.0)),   # config 1
     (2048, 16, 1e-6, "jitter", "dft", 0, {}),                                            # odd L
     (2048, 8, 1e-6, "uniform", "fio", 1, {}),                                            # Example 1
+    (4096, 64, 1e-6, "schlomilch", "j0", 0, dict(oversample=2.0, oversample_leaf=4.0)),  # Example 2
 ])
 def test_accuracy_against_dense(N, n0, eps, grid, kind, prof, kw):
-    x, xi = inputs.uniform_grid(N) if grid == "uniform" else inputs.jittered_grid(N, seed=N)
+    x, xi = {"uniform": inputs.uniform_grid, "schlomilch": inputs.schlomilch_grid}.get(
+        grid, lambda n: inputs.jittered_grid(n, seed=n))(N)
     plan = P.Plan.build(x, xi, eps=eps, leaf=n0, kernel=kind, c_profile=prof, sign=-1, **kw)
-    K = kernels.Kernel(kernels.KIND_FIO if kind == "fio" else kernels.KIND_DFT, sign=-1, c_profile=prof)
+    kinds = {"fio": kernels.KIND_FIO, "dft": kernels.KIND_DFT, "j0": kernels.KIND_J0}
+    K = kernels.Kernel(kinds[kind], sign=-1, c_profile=prof)
     g = inputs.complex_gaussian(N, 1, seed=5)[:, 0]
     ud = idbf.dense_matvec(K, x, xi, g)
     gd = torch.from_numpy(g).cuda()
@@ -119,3 +122,25 @@ def test_checkpoint_of_a_built_plan(tmp_path):
     p2 = P.Plan.load(path, storage=P.STORE_DF64)
     g = torch.from_numpy(inputs.complex_gaussian(N, 1, seed=9)[:, 0]).cuda()
     assert rel(p2.apply(g, mode=P.MODE_DF64).cpu().numpy(), plan.apply(g).cpu().numpy()) < 1e-13
+
+
+def test_cuda_j0_entries_match_the_host_routine():
+    # Example 2's entries come from CUDA's j0 on the device and scipy's j0 in the oracle. CUDA
+    # documents j0's error as at most 7 ulp for |x| < 8 and 5e-12 absolute beyond (arguments
+    # here reach N pi); scipy's is far smaller. So each row of the direct matvec u^d (every
+    # entry of the row enters) may differ by at most 5e-12 sum_j |g_j| plus the rounding of two
+    # FP64 sums of N terms.
+    N = 4096
+    x, xi = inputs.schlomilch_grid(N)
+    K = kernels.Kernel(kernels.KIND_J0)
+    g = inputs.complex_gaussian(N, 1, seed=9)[:, 0]
+    rows = np.arange(0, N, 97)
+    ref = idbf.dense_matvec(K, x, xi, g, rows=rows)
+    got = P.kernel_matvec_rows(torch.from_numpy(x).cuda(), torch.from_numpy(xi).cuda(), torch.from_numpy(g).cuda(),
+                               torch.from_numpy(rows.astype(np.int64)).cuda(), kernel="j0")
+    got = got.cpu().numpy()
+    absK = np.abs(K.entries(x, xi, rows, np.arange(N)))
+    bound = 5e-12 * np.abs(g).sum() + 2 * N * 2.0 ** -53 * (absK @ np.abs(g))
+    assert np.all(np.abs(got - ref) <= bound)
+    assert rel(got, ref) < 1e-11
+

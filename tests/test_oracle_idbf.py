@@ -170,3 +170,17 @@ def test_invalid_sizes_are_rejected():
     x, xi = inputs.uniform_grid(16)
     with pytest.raises(ValueError):
         idbf.build(kernels.Kernel(), x, xi, 1e-6, 8)      # L = 1
+
+
+def test_schlomilch_example2_meets_eps():
+    # Example 2: J_0 on x_k = (k-1)/N, xi_n = n pi with k = min{m, n}. Like the benchmarked FIO
+    # kernel, J_0(x xi) ~ sqrt(2/(pi x xi)) cos(x xi - pi/4) oscillates across a block, and the
+    # Mock-Chebyshev samples need oversampling t = 2 (t = 4 at the leaves) to reach eps.
+    N, n0, eps = 2048, 16, 1e-8
+    x, xi = inputs.schlomilch_grid(N)
+    K = kernels.Kernel(kernels.KIND_J0)
+    F = idbf.build(K, x, xi, eps, n0, t=2, t_leaf=4)
+    g = inputs.complex_gaussian(N, 2, seed=4)
+    ref = K.entries(x, xi, np.arange(N), np.arange(N)) @ g
+    assert idbf.relative_error(idbf.apply(F, g), ref) < 10 * eps
+

@@ -77,3 +77,27 @@ def test_frac_prod_keeps_low_order_bits():
 def test_golden_files_exist():
     here = os.path.join(os.path.dirname(__file__), "golden")
     assert os.path.exists(os.path.join(here, "splitmix64.txt"))
+
+
+def test_j0_kernel_values_and_integral_representation():
+    # Example 2 (Eq. S): K(x, xi) = J_0(x xi). Pinned independently of scipy's routine by
+    # published values (Abramowitz and Stegun, Tables 9.1 and 9.5: J_0(1) and the first zero
+    # j_{0,1}) and by Bessel's integral J_0(z) = (1/pi) int_0^pi cos(z sin t) dt, evaluated with
+    # the trapezoidal rule on 4096 points (exponentially accurate for this periodic integrand).
+    K = kernels.Kernel(kernels.KIND_J0)
+    one = np.array([1.0])
+    assert K.entries(np.array([0.0]), one, [0], [0])[0, 0] == 1.0
+    assert abs(K.entries(one, one, [0], [0])[0, 0] - 0.7651976865579666) < 1e-15
+    assert abs(K.entries(np.array([2.404825557695773]), one, [0], [0])[0, 0]) < 1e-15
+    N = 64
+    x, xi = inputs.schlomilch_grid(N)
+    assert x[0] == 0.0 and x[1] == 1.0 / N and xi[0] == math.pi and xi[-1] == N * math.pi
+    rows, cols = np.arange(0, N, 5), np.arange(0, N, 3)
+    A = K.entries(x, xi, rows, cols)
+    assert np.all(A.imag == 0)
+    t = np.linspace(0.0, np.pi, 4097)
+    w = np.full(t.size, np.pi / 4096)
+    w[0] = w[-1] = np.pi / 8192
+    Z = np.outer(x[rows], xi[cols])
+    ref = (np.cos(Z[:, :, None] * np.sin(t)[None, None, :]) * w).sum(axis=2) / np.pi
+    assert np.max(np.abs(A.real - ref)) < 1e-13
