@@ -325,6 +325,13 @@ def gpu_arm(args, rank, world, local):
         modes[name] = {"applies_per_s": n / secs, "ms_per_apply": secs / n * 1e3,
                        "algorithmic_GBps": ab * n / secs / 1e9,
                        "rel_err_vs_fp64": 0.0 if name == "fp64" else rel_32}
+        if name == "fp64":
+            # the FP64 apply is bound by the FP64 FMA pipes: 4 DFMA per stored complex entry
+            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            dpk = sms * 2 * 2070e6 / 1e12  # 2 FP64 FMA per SM per clock (1.25 TFLOP/s nominal) x max clock
+            dfma = 4.0 * plan.stats()["entries"] * n / secs / 1e12
+            modes[name]["alu"] = {"achieved_TDFMA_per_s": dfma, "peak_TDFMA_per_s": dpk, "frac": dfma / dpk,
+                                  "peak_kind": f"derived: {sms} SMs x 2 FP64 FMA/clk x 2070 MHz"}
     # headline: double-float, clocks sampled during the timed region
     with ClockSampler(torch.cuda.current_device()) as cs:
         secs = timed(P.MODE_DF64, gd, args.steps, args.warmup)
