@@ -53,7 +53,8 @@ constexpr uint32_t RAW_BYTES = RAWV * NT * 8;          // one raw chunk: 16 KB, 
 constexpr int GIXCAP = 1024;     // columns per block supported (gather indices in shared memory)
 constexpr size_t RAW_OFF = NSTAGE * (size_t)STAGE;
 constexpr size_t GIX_OFF = RAW_OFF + PFR * (size_t)RAW_BYTES;
-constexpr size_t BAR_OFF = GIX_OFF + GIXCAP * sizeof(int32_t);
+constexpr size_t QIX_OFF = GIX_OFF + GIXCAP * sizeof(int32_t);
+constexpr size_t BAR_OFF = QIX_OFF + MAXROWS * sizeof(int32_t);
 constexpr size_t SMEM = BAR_OFF + 128;                 // stages, raw ring, indices, barriers
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t D_CORR = NACC * NH;                 // TMEM column of the correction accumulator
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(NT + 32, 1)
   uint64_t* full = (uint64_t*)(sm + BAR_OFF);
   float2* raw = (float2*)(sm + RAW_OFF);     // [PFR][RAWV][NT]: each thread's own values
   int32_t* gix = (int32_t*)(sm + GIX_OFF);   // node-input element of each column of the block
+  int32_t* qix = (int32_t*)(sm + QIX_OFF);   // per block row: V pass-through element, U output element
   uint64_t* empty = full + NSTAGE;
   uint64_t* done = empty + NSTAGE;
   uint64_t* tfree = done + 1;
@@ -275,6 +277,8 @@ __global__ void __launch_bounds__(NT + 32, 1)
       if (!mma_warp) {  // column k of the block multiplies node-input element gix[k]
         staging_sync();  // the previous block's copies are all issued
         for (int k = tid; k < cols; k += NT) gix[k] = g_elem(k);
+        if (d.kind != KIND_S)
+          for (int r = tid; r < rows; r += NT) qix[r] = d.kind == KIND_V ? ix[r] : ix[(c ? l1 : l0) + r];
         staging_sync();
       }
       const int nkc = (cols + KC - 1) / KC;
@@ -374,15 +378,31 @@ __global__ void __launch_bounds__(NT + 32, 1)
           }
           cp_async_wait<0>();
           kcg += (uint32_t)nkc;
-          // ---- epilogue: lane quadrant of warp w % 4 = 32 rhs; warps w and w + 4 split the columns
+          // ---- epilogue: lane quadrant of warp w % 4 = 32 rhs; warps w and w + 4 split the columns.
+          // The terms added to the products (V: the pass-through input u[q]; U, block 1: block 0's
+          // output) do not depend on the MMAs: they are loaded one column group ahead, the first
+          // group before the wait for the pass's MMAs.
+          const int q = warp & 3, half = warp >> 2;
+          const int n = rt * MR + q * 32 + lane;
+          float2 pre[8], nxt[8];
+          auto load_terms = [&](int c0, float2 (&tv)[8]) {
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+              tv[h] = make_float2(0.f, 0.f);
+              const int r = r0 + (c0 >> 1) + h;
+              if (failed || n >= R || c0 >= nreal || (c0 >> 1) + h >= prow) continue;
+              if (d.kind == KIND_V) tv[h] = in_at(qix[r], n);
+              else if (d.kind == KIND_U && c == 1) tv[h] = *out_ptr(qix[r], n);
+            }
+          };
+          load_terms(half * 16, pre);
           if (!failed && !wait_abortable(done, passes & 1, limit_ns, abortp)) fail();
           if (__any_sync(0xffffffffu, failed)) failed = true;  // warp-uniform from here (tcgen05.ld)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           if (!failed) {
-            const int q = warp & 3, half = warp >> 2;
-            const int n = rt * MR + q * 32 + lane;
             const int nacc = min(NACC, nkc);  // main accumulators written in this pass
             for (int c0 = half * 16; c0 < nreal; c0 += 32) {
+              load_terms(c0 + 32, nxt);
               const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
               uint32_t v[16], w[16];
               float acc[16];
@@ -399,23 +419,18 @@ __global__ void __launch_bounds__(NT + 32, 1)
               }
 #pragma unroll
               for (int e = 0; e < 16; ++e) acc[e] += __uint_as_float(w[e]);
-              if (n >= R) continue;
+              if (n < R) {
 #pragma unroll
-              for (int h = 0; h < 8; ++h) {
-                const int r = r0 + (c0 >> 1) + h;  // complex output row of the block
-                if ((c0 >> 1) + h >= prow) break;
-                const float2 res = make_float2(acc[2 * h], acc[2 * h + 1]);
-                if (d.kind == KIND_V) {
-                  const float2 uq = in_at(ix[r], n);
-                  *out_ptr((c ? len_o0 : 0) + r, n) = make_float2(res.x + uq.x, res.y + uq.y);
-                } else if (d.kind == KIND_S) {
-                  *out_ptr((c ? len_o0 : 0) + r, n) = res;
-                } else {
-                  float2* pp = out_ptr(ix[(c ? l1 : l0) + r], n);
-                  if (c == 0) *pp = res;
-                  else { const float2 a = *pp; *pp = make_float2(a.x + res.x, a.y + res.y); }
+                for (int h = 0; h < 8; ++h) {
+                  const int r = r0 + (c0 >> 1) + h;  // complex output row of the block
+                  if ((c0 >> 1) + h >= prow) break;
+                  const float2 res = make_float2(acc[2 * h] + pre[h].x, acc[2 * h + 1] + pre[h].y);
+                  if (d.kind == KIND_U) *out_ptr(qix[r], n) = res;  // block 1: pre = block 0's term
+                  else *out_ptr((c ? len_o0 : 0) + r, n) = res;
                 }
               }
+#pragma unroll
+              for (int h = 0; h < 8; ++h) pre[h] = nxt[h];
             }
           }
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
