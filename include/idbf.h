@@ -271,6 +271,14 @@ idbf_status idbf_batch_info(idbf_batch b, int32_t* rhs_per_item, int32_t* nodes_
  * gave up since the last call (its results are invalid), IDBF_OK otherwise. */
 idbf_status idbf_batch_sync_status(idbf_batch b, void* stream);
 
+/* idbf_batch_debug_set_wait - fault injection for tests: set the time limit of the batch
+ * kernel's dependency waits (default 2 s) and, with extra_target > 0, raise the completion count
+ * that the first operator's level-1 items wait for above the number of level-0 items, so that
+ * those waits run out (a failure made on the host: no device fault). Each such item is then
+ * skipped and counted as done, and idbf_batch_sync_status reports IDBF_ETIMEOUT. (limit, 0)
+ * restores normal operation. Re-captures the graph. Not for production use. */
+idbf_status idbf_batch_debug_set_wait(idbf_batch b, uint64_t limit_ns, int32_t extra_target);
+
 /* idbf_batch_destroy - release the batch (synchronises the device first; NULL is a no-op). */
 void idbf_batch_destroy(idbf_batch b);
 

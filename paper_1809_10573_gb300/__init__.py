@@ -239,6 +239,11 @@ class Batch:
     def set_tiling(self, tile: int, nodes_per_item: int = 1):
         _lib.check(_lib.lib().idbf_batch_set_tiling(self._h, int(tile), int(nodes_per_item)), "idbf_batch_set_tiling")
 
+    def debug_set_wait(self, limit_ns: int, extra_target: int = 0):
+        """Fault injection for tests (idbf_batch_debug_set_wait in include/idbf.h)."""
+        _lib.check(_lib.lib().idbf_batch_debug_set_wait(self._h, int(limit_ns), int(extra_target)),
+                   "idbf_batch_debug_set_wait")
+
     def info(self) -> dict:
         a, b, c, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         _lib.check(_lib.lib().idbf_batch_info(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "idbf_batch_info")

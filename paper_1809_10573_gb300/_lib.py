@@ -75,6 +75,7 @@ SIGNATURES = {
     "idbf_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
                                       C.POINTER(C.c_float)]),
     "idbf_batch_set_tiling": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "idbf_batch_debug_set_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32]),
     "idbf_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32)]),
     "idbf_batch_sync_status": (C.c_int, [C.c_void_p, C.c_void_p]),

@@ -165,6 +165,7 @@ struct idbf_batch_s {
   size_t smem = 0;
   int ctas = 0;
   uint64_t limit_ns = 2000000000ull;
+  int debug_extra = 0;  // fault injection: added to the first operator's level-0 completion target
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;
@@ -308,6 +309,7 @@ idbf_status layout(idbf_batch_s* b) {
         }
     }
   b->nitems = (int)items.size();
+  if (b->debug_extra > 0 && b->nlevels_total > 0) target[0] += b->debug_extra;
   if (!tile_valid(b->mode, b->tile)) return IDBF_EUNSUPPORTED;
   b->smem = IDBF_BATCH_DISPATCH(smem_for, (size_t)0, b);
   if (b->smem == 0 || b->smem > 200 * 1024) return IDBF_EUNSUPPORTED;
@@ -489,6 +491,13 @@ idbf_status idbf_batch_set_tiling(idbf_batch b, int32_t tile, int32_t nodes_per_
     return r == IDBF_OK ? s : r;
   }
   return s;
+}
+
+idbf_status idbf_batch_debug_set_wait(idbf_batch b, uint64_t limit_ns, int32_t extra_target) {
+  if (!b || limit_ns == 0 || extra_target < 0) return IDBF_EINVAL;
+  b->limit_ns = limit_ns;
+  b->debug_extra = extra_target;
+  return layout(b);  // the limit and the targets are captured in the graph
 }
 
 idbf_status idbf_batch_info(idbf_batch b, int32_t* rhs_per_item, int32_t* nodes_per_item, int32_t* items, int32_t* ctas) {

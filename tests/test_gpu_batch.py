@@ -81,3 +81,29 @@ def test_batch_with_gpu_built_plans_of_uneven_size():
     b.sync_status()
     for y, p, x in zip(ys, plans, xs):
         assert rel(y.cpu().numpy(), p.apply(x, mode=P.MODE_DF64).cpu().numpy()) < 1e-13
+
+
+def test_batch_wait_that_runs_out_reports_a_timeout_and_the_batch_recovers():
+    # failure made on the host: the first operator's level-1 items wait for one more level-0
+    # completion than there are level-0 items, so their bounded waits (20 ms) run out; the
+    # status reports it, and with the target restored the same batch gives correct results
+    plans, xs, refs = [], [], []
+    for k, (case, r) in enumerate(CASES[:3]):
+        c = oracle_case(case)
+        plans.append(P.Plan.import_factors(c["ex"], storage=P.STORE_C64))
+        X = inputs.complex_gaussian(c["N"], r, seed=70 + k)
+        xs.append(torch.from_numpy(X.astype(np.complex64)).cuda())
+        refs.append(idbf.apply(c["F"], X))
+    b = P.Batch(plans, [r for _, r in CASES[:3]], mode=P.MODE_FP32)
+    b.debug_set_wait(20_000_000, 1)
+    b.apply(xs)
+    with pytest.raises(P.IDBFError) as e:
+        b.sync_status()
+    assert e.value.status == _lib.ETIMEOUT
+    b.debug_set_wait(2_000_000_000, 0)
+    ys = b.apply(xs)
+    b.sync_status()
+    for y, ref in zip(ys, refs):
+        assert rel(y.cpu().numpy(), ref) < 2e-5
+    b.close()
+
