@@ -462,6 +462,8 @@ def gpu_batch(args, rank, world):
     import paper_1809_10573_gb300 as P
     from paper_1809_10573_gb300 import inputs
     ops = inputs.uneven_batch(seed=4)
+    if args.log2n is not None:  # a smaller batch for profiling: the same draw, N capped at 2^log2n
+        ops = [dict(o, N=min(o["N"], 1 << args.log2n)) for o in ops]
     plans, xs = [], []
     t0 = time.time()
     for o in ops:
@@ -523,7 +525,8 @@ def gpu_batch(args, rank, world):
             "value": value, "unit": "batches/s (64 operator applies each)", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "64 ops, seed 4: FIO (ops 0-31) / jittered DFT (32-63), eps=1e-6, leaf 64, complex64 factors"},
+            "config": {"workload": "64 ops, seed 4: FIO (ops 0-31) / jittered DFT (32-63), eps=1e-6, leaf 64, complex64 factors"
+                                   + (f", N capped at 2^{args.log2n}" if args.log2n is not None else "")},
             "rel_err": {"max_over_ops_vs_fp64": r32["max_rel_err_vs_fp64"]},
             "operator_applies_per_s": 64 * value, "vector_applies_per_s": sum(o["nrhs"] for o in ops) * value,
             # 1-32 right-hand sides make ~8 FMA per factor byte: the FP32 FMA pipes, not HBM, bound it
