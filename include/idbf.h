@@ -247,17 +247,19 @@ idbf_status idbf_batch_create(const idbf_plan* plans, int32_t nops, const int64_
 idbf_status idbf_batch_apply(idbf_batch b, const void* const* x, void* const* y, const int64_t* ld,
                              void* stream);
 
-/* idbf_batch_autotune - time the batch for every tile (right-hand sides per work item and per
- * thread: (1,1), (4,2), (8,2), (8,4), and in FP32 also (16,4), (32,8)) and nodes per item in
- * {1, 2, 4} (reps launches each, on the given buffers; tiles whose shared memory exceeds 200 KB
- * are skipped) and keep the fastest; *best_ms receives its time per launch. Synchronous. */
+/* idbf_batch_autotune - time the batch for every tiling of idbf_batch_set_tiling below (for the
+ * mixed tiling 7 also its row threshold in {32, 64, 96, 128, 192}) and nodes per item in
+ * {1, 2, 4} (reps launches each, on the given buffers; tilings whose shared memory exceeds
+ * 200 KB are skipped) and keep the fastest; *best_ms receives its time per launch. Synchronous. */
 idbf_status idbf_batch_autotune(idbf_batch b, const void* const* x, void* const* y, const int64_t* ld,
                                 int32_t reps, void* stream, float* best_ms);
 
 /* idbf_batch_set_tiling - choose the tiling by hand: `tile` indexes the autotuner's list above
  * (0: (1,1), 1: (4,2), 2: (8,2), 3: (8,4) per-thread right-hand sides; 4: 8 and 5: 16 right-hand
- * sides per item in 4 x 4 register tiles over streamed factor columns, 6: 32 in 4 x 8 tiles; 4-6
- * in FP32 and FP64 only, 6 in FP32 only), nodes_per_item in {1, 2, 4}. IDBF_EUNSUPPORTED if the
+ * sides per item in 4 x 4 register tiles over streamed factor columns, 6: 32 in 4 x 8 tiles;
+ * 7: mixed per level, 16 per item in register tiles where a level's blocks have more than a row
+ * threshold (64 unless the autotuner chose another), else 8 per item, 4 per thread; 4-7 in FP32
+ * and FP64 only, 6 in FP32 only), nodes_per_item in {1, 2, 4}. IDBF_EUNSUPPORTED if the
  * tile does not exist for the batch's precision or its shared memory exceeds 200 KB (the
  * previous tiling is then kept), IDBF_EINVAL for other values. Synchronous. */
 idbf_status idbf_batch_set_tiling(idbf_batch b, int32_t tile, int32_t nodes_per_item);

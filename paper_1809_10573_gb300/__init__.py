@@ -234,7 +234,7 @@ class Batch:
         return ms.value
 
     # tile indices of idbf_batch_set_tiling: (right-hand sides per item, per thread, register-tile width)
-    TILES = ((1, 1, 0), (4, 2, 0), (8, 2, 0), (8, 4, 0), (8, 0, 4), (16, 0, 4), (32, 0, 8))
+    TILES = ((1, 1, 0), (4, 2, 0), (8, 2, 0), (8, 4, 0), (8, 0, 4), (16, 0, 4), (32, 0, 8), (16, 4, -1))
 
     def set_tiling(self, tile: int, nodes_per_item: int = 1):
         _lib.check(_lib.lib().idbf_batch_set_tiling(self._h, int(tile), int(nodes_per_item)), "idbf_batch_set_tiling")

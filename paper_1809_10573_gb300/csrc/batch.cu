@@ -29,7 +29,8 @@ namespace bat {
 struct OpLevel {
   DevLevel d;
   const void* mat;
-  int gcap, rcap, max_in, max_out, max_rows, pad;
+  int gcap, rcap, max_in, max_out, max_rows;
+  int body;  // mixed tiling: 1 = tiled body (16 right-hand sides per item), 0 = per-thread body (8)
 };
 struct OpDesc {
   int L, R, level_base, pad;
@@ -50,12 +51,15 @@ constexpr int NT = 256;
 
 // Tiles: right-hand sides per work item (RB); then either right-hand sides per thread (RPT, the
 // per-node body fwd_node, all precisions) or TC > 0: the tiled body fwd_node_tiled with TR x TC
-// register tiles and streamed factor columns (FP32 and FP64).
+// register tiles and streamed factor columns (FP32 and FP64), or TC < 0: mixed, per level: the
+// tiled body with 16 right-hand sides per item where the level's blocks have more than a
+// threshold of rows, else the per-thread body with 8 per item, 4 per thread (FP32 and FP64).
 struct Tile {
   int rb, rpt, tc;
 };
-constexpr Tile kTiles[] = {{1, 1, 0}, {4, 2, 0}, {8, 2, 0}, {8, 4, 0}, {8, 0, 4}, {16, 0, 4}, {32, 0, 8}};
-constexpr int kNumTiles = 7;
+constexpr Tile kTiles[] = {{1, 1, 0}, {4, 2, 0}, {8, 2, 0}, {8, 4, 0}, {8, 0, 4}, {16, 0, 4}, {32, 0, 8}, {16, 4, -1}};
+constexpr int kNumTiles = 8;
+constexpr int kMixedSmallRB = 8;
 template <class P>
 __host__ __device__ constexpr int max_rb() {
   return std::is_same<P, FP32P>::value ? 32 : std::is_same<P, FP64P>::value ? 16 : 8;
@@ -118,12 +122,20 @@ __global__ void __launch_bounds__(NT, TC == 8 ? 1 : 2) k_batch(const OpDesc* __r
       io.wout = w.level < od.L ? wb[w.level & 1] : nullptr;
       for (int n = 0; n < w.nodes; ++n) {
         if (n) __syncthreads();
-        if constexpr (TC > 0)
+        if constexpr (TC > 0) {
           fwd_node_tiled<P, RB, TC>(ol.d, (const typename P::mat_t*)ol.mat, io, ol.max_rows, ol.max_in, ol.max_out,
                                     (int64_t)(w.node0 + n), w.r0, smem);
-        else
+        } else if constexpr (TC < 0) {
+          if (ol.body)
+            fwd_node_tiled<P, RB, 4>(ol.d, (const typename P::mat_t*)ol.mat, io, ol.max_rows, ol.max_in, ol.max_out,
+                                     (int64_t)(w.node0 + n), w.r0, smem);
+          else
+            fwd_node<P, kMixedSmallRB, RPT>(ol.d, (const typename P::mat_t*)ol.mat, io, ol.gcap, ol.rcap, ol.max_in,
+                                            (int64_t)(w.node0 + n), w.r0, smem);
+        } else {
           fwd_node<P, RB, RPT>(ol.d, (const typename P::mat_t*)ol.mat, io, ol.gcap, ol.rcap, ol.max_in,
                                (int64_t)(w.node0 + n), w.r0, smem);
+        }
       }
     }
     __threadfence();  // release: this item's outputs before its completion count
@@ -133,11 +145,14 @@ __global__ void __launch_bounds__(NT, TC == 8 ? 1 : 2) k_batch(const OpDesc* __r
 }
 
 template <class P, int RB, int RPT, int TC>
-size_t node_smem(const LevelInfo& li) {
+size_t node_smem(const LevelInfo& li, bool tiled_body) {
   const int gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
   const int rcap = std::max(li.max_rows, li.max_cols);
   if constexpr (TC > 0)
     return tiled::smem_bytes<P, RB, TC>(li.max_in, li.max_out, li.max_rows, NT);
+  else if constexpr (TC < 0)
+    return tiled_body ? tiled::smem_bytes<P, RB, 4>(li.max_in, li.max_out, li.max_rows, NT)
+                      : fwd_node_smem<P, kMixedSmallRB, RPT>(li.max_in, gcap, rcap, NT);
   else
     return fwd_node_smem<P, RB, RPT>(li.max_in, gcap, rcap, NT);
 }
@@ -162,6 +177,8 @@ struct idbf_batch_s {
   int* d_status = nullptr;
   void** d_ptrs = nullptr;    // xs[nops], ys[nops], then lds[nops] (int64)
   int tile = 1, rb = 4, npi = 1;  // tile: index into bat::kTiles
+  int mix_rows = 64;              // mixed tiling: levels with at most this many rows per block use the per-thread body
+  std::vector<bat::OpLevel> h_lv; // host copy of the level table (the body flags change with mix_rows)
   size_t smem = 0;
   int ctas = 0;
   uint64_t limit_ns = 2000000000ull;
@@ -217,7 +234,8 @@ size_t smem_for(idbf_batch_s* b) {
   } else {
     size_t sm = 0;
     for (int o = 0; o < b->nops; ++o)
-      for (const LevelInfo& li : b->plans[o]->p.lv) sm = std::max(sm, bat::node_smem<P, RB, RPT, TC>(li));
+      for (const LevelInfo& li : b->plans[o]->p.lv)
+        sm = std::max(sm, bat::node_smem<P, RB, RPT, TC>(li, li.max_rows > b->mix_rows));
     return sm;
   }
 }
@@ -244,19 +262,19 @@ int occupancy(idbf_batch_s* b) {
           case 0: return FN<FP64P, 0>(__VA_ARGS__); case 1: return FN<FP64P, 1>(__VA_ARGS__);  \
           case 2: return FN<FP64P, 2>(__VA_ARGS__); case 3: return FN<FP64P, 3>(__VA_ARGS__);  \
           case 4: return FN<FP64P, 4>(__VA_ARGS__); case 5: return FN<FP64P, 5>(__VA_ARGS__);  \
-          case 6: return FN<FP64P, 6>(__VA_ARGS__);                                            \
+          case 6: return FN<FP64P, 6>(__VA_ARGS__); case 7: return FN<FP64P, 7>(__VA_ARGS__);  \
           default: return RET_ON_BAD; }                                                        \
       case IDBF_MODE_DF64: switch (b->tile) {                                                  \
           case 0: return FN<DF64P, 0>(__VA_ARGS__); case 1: return FN<DF64P, 1>(__VA_ARGS__);  \
           case 2: return FN<DF64P, 2>(__VA_ARGS__); case 3: return FN<DF64P, 3>(__VA_ARGS__);  \
           case 4: return FN<DF64P, 4>(__VA_ARGS__); case 5: return FN<DF64P, 5>(__VA_ARGS__);  \
-          case 6: return FN<DF64P, 6>(__VA_ARGS__);                                            \
+          case 6: return FN<DF64P, 6>(__VA_ARGS__); case 7: return FN<DF64P, 7>(__VA_ARGS__);  \
           default: return RET_ON_BAD; }                                                        \
       default: switch (b->tile) {                                                              \
           case 0: return FN<FP32P, 0>(__VA_ARGS__); case 1: return FN<FP32P, 1>(__VA_ARGS__);  \
           case 2: return FN<FP32P, 2>(__VA_ARGS__); case 3: return FN<FP32P, 3>(__VA_ARGS__);  \
           case 4: return FN<FP32P, 4>(__VA_ARGS__); case 5: return FN<FP32P, 5>(__VA_ARGS__);  \
-          case 6: return FN<FP32P, 6>(__VA_ARGS__);                                            \
+          case 6: return FN<FP32P, 6>(__VA_ARGS__); case 7: return FN<FP32P, 7>(__VA_ARGS__);  \
           default: return RET_ON_BAD; }                                                        \
     }                                                                                          \
   }()
@@ -280,6 +298,11 @@ idbf_status layout(idbf_batch_s* b) {
   free_layout(b);
   if (!tile_valid(b->mode, b->tile)) return IDBF_EUNSUPPORTED;
   b->rb = bat::kTiles[b->tile].rb;
+  const bool mixed = bat::kTiles[b->tile].tc < 0;
+  // level bodies of the mixed tiling (ignored by the others)
+  for (int o = 0, li = 0; o < b->nops; ++o)
+    for (const LevelInfo& lvi : b->plans[o]->p.lv) b->h_lv[li++].body = lvi.max_rows > b->mix_rows ? 1 : 0;
+  IDBF_CUDA_TRY(cudaMemcpy(b->d_lv, b->h_lv.data(), sizeof(bat::OpLevel) * b->h_lv.size(), cudaMemcpyHostToDevice));
   std::vector<bat::Item> items;
   std::vector<int> target(b->nlevels_total, 0);
   int maxL = 0, base = 0;
@@ -295,8 +318,9 @@ idbf_status layout(idbf_batch_s* b) {
       if (l > p.L) continue;
       // the right-hand-side blocks of a run of nodes are neighbours in the queue, so the
       // blocks' second and later reads of the factors come from L2
+      const int rbl = mixed && !b->h_lv[lbase[o] + l].body ? bat::kMixedSmallRB : b->rb;
       for (int n0 = 0; n0 < p.m; n0 += b->npi)
-        for (int r0 = 0; r0 < b->R[o]; r0 += b->rb) {
+        for (int r0 = 0; r0 < b->R[o]; r0 += rbl) {
           bat::Item it;
           it.op = o;
           it.level = l;
@@ -384,7 +408,7 @@ idbf_status idbf_batch_create(const idbf_plan* plans, int32_t nops, const int64_
       ol.max_in = li.max_in;
       ol.max_out = li.max_out;
       ol.max_rows = li.max_rows;
-      ol.pad = 0;
+      ol.body = 1;
       lvs.push_back(ol);
     }
   }
@@ -396,6 +420,7 @@ idbf_status idbf_batch_create(const idbf_plan* plans, int32_t nops, const int64_
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_ops, ods.data(), sizeof(bat::OpDesc) * nops, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_lv, lvs.data(), sizeof(bat::OpLevel) * lvs.size(), cudaMemcpyHostToDevice);
+    b->h_lv = lvs;
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) { set_cuda_error(e); s = e == cudaErrorMemoryAllocation ? IDBF_ENOMEM : IDBF_ECUDA; }
@@ -446,14 +471,18 @@ idbf_status idbf_batch_autotune(idbf_batch b, const void* const* x, void* const*
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int btile = b->tile, bnpi = b->npi;
+  int btile = b->tile, bnpi = b->npi, bmix = b->mix_rows;
   const int npis[3] = {1, 2, 4};
+  const int mixes[5] = {32, 64, 96, 128, 192};  // mixed tiling: row threshold of the per-thread body
   idbf_status s = IDBF_OK;
   for (int a = 0; a < bat::kNumTiles && s == IDBF_OK; ++a)
-    for (int c = 0; c < 3 && s == IDBF_OK; ++c) {
+    for (int c = 0; c < 3 * 5 && s == IDBF_OK; ++c) {
       if (!tile_valid(b->mode, a)) continue;
+      const bool mixed = bat::kTiles[a].tc < 0;
+      if (!mixed && c >= 3) continue;
       b->tile = a;
-      b->npi = npis[c];
+      b->npi = npis[c % 3];
+      b->mix_rows = mixed ? mixes[c / 3] : bmix;
       idbf_status r = layout(b);
       if (r == IDBF_EUNSUPPORTED) continue;
       if (r != IDBF_OK) { s = r; break; }
@@ -465,12 +494,13 @@ idbf_status idbf_batch_autotune(idbf_batch b, const void* const* x, void* const*
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= reps;
-      if (ms < best) { best = ms; btile = b->tile; bnpi = b->npi; }
+      if (ms < best) { best = ms; btile = b->tile; bnpi = b->npi; bmix = b->mix_rows; }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->tile = btile;
   b->npi = bnpi;
+  b->mix_rows = bmix;
   if (s == IDBF_OK) s = layout(b);
   if (best_ms) *best_ms = best;
   return s;
