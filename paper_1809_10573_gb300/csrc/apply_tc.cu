@@ -18,12 +18,12 @@
 // correction products (~2^-11 of the main ones, which would lose their low bits in the main
 // accumulators) to a fourth; the four are summed in round-to-nearest FP32 in the epilogue. With
 // 4 x 128 TMEM columns a pass covers 128 real (64 complex) output rows; a block takes up to four
-// passes. Eight warps stage the operands into shared memory in the K-major, no-swizzle canonical
-// layout (8-row x 16-byte core matrices), each thread writing 16 bytes (two complex columns of
-// one row) so that a warp's stores fill 512 contiguous bytes, with the global loads of the next
-// two chunks in flight; four stages over K. A ninth warp issues the MMAs as soon as a stage is
-// full (mbarrier), and tcgen05.commit frees the stage; the staging warps read the accumulators
-// out after each pass.
+// passes. Eight warps stage the operands: each thread copies with cp.async, four chunks ahead,
+// exactly the values it later converts, splits them into TF32 hi / lo and stores them in the
+// K-major, no-swizzle canonical layout (8-row x 16-byte core matrices), 16 bytes at a time (two
+// complex columns of one row) so that a warp's stores fill 512 contiguous bytes; four stages
+// over K. A ninth warp issues the MMAs as soon as a stage is full (mbarrier), and
+// tcgen05.commit frees the stage; the staging warps read the accumulators out after each pass.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,8 +46,8 @@ constexpr uint32_t B_BYTES = NH * 2 * KC * 4;     // 8 KB
 constexpr uint32_t LBO_A = (MR / 8) * 128;        // byte step between 4-element K groups
 constexpr uint32_t LBO_B = (NH / 8) * 128;
 constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;  // hi and lo of both operands: 32 KB
-constexpr int NSTAGE = 3;
-constexpr int PFR = 6;           // chunks whose global operands are in flight (cp.async raw ring)
+constexpr int NSTAGE = 4;
+constexpr int PFR = 4;           // chunks whose global operands are in flight (cp.async raw ring)
 constexpr int RAWV = 8;          // raw complex values per thread per chunk (A: 2 items x 2, B: 2 x 2)
 constexpr uint32_t RAW_BYTES = RAWV * NT * 8;          // one raw chunk: 16 KB, value-major
 constexpr int GIXCAP = 1024;     // columns per block supported (gather indices in shared memory)
