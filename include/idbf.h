@@ -57,7 +57,7 @@ typedef enum {
   IDBF_ERANKCAP = 4,     /* warning: some ID stopped at its maximum rank min(k, samples) with columns left (accuracy may exceed eps) */
   IDBF_ETIMEOUT = 5,     /* a bounded device-side wait gave up; the results of the call are invalid */
   IDBF_EFORMAT = 6,      /* factor arrays or a saved file are inconsistent */
-  IDBF_EUNSUPPORTED = 7  /* valid request this build does not handle (e.g. storage absent for a mode) */
+  IDBF_EUNSUPPORTED = 7  /* valid request the library does not handle (e.g. storage absent for a mode) */
 } idbf_status;
 
 /* ---- kernels (the numerical examples of Sec. 3) ---------------------------------------- */

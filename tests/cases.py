@@ -11,7 +11,7 @@ CASES = {
     # name: (N, n0, kernel, grid, eps, build kwargs)
     "dft_1024": (1024, 16, ("dft", -1, 0), "uniform", 1e-8, {}),
     "dft_jit_2048_oddL": (2048, 16, ("dft", -1, 0), "jitter", 1e-6, {}),            # L = 7
-    "fio_base_4096": (4096, 64, ("fio", 0, 0), "uniform", 1e-8, dict(t=2, t_leaf=4)),  # config 1
+    "fio_base_4096": (4096, 64, ("fio", 0, 0), "uniform", 1e-8, dict(t=2, t_leaf=4)),  # N = 4096, eps = 1e-8 FIO
     "fio_paper_2048": (2048, 8, ("fio", 0, 1), "uniform", 1e-6, {}),                # Example 1, L = 8
     "fio_base_8192_oddL": (8192, 64, ("fio", 0, 0), "uniform", 1e-6, dict(t=2, t_leaf=4)),  # L = 7
     "j0_2048": (2048, 16, ("j0", 0, 0), "schlomilch", 1e-8, dict(t=2, t_leaf=4)),   # Example 2, L = 7

@@ -48,7 +48,7 @@ def test_exact_mode_dft():
 
 
 @pytest.mark.parametrize("N,n0,eps,grid,kind,prof,kw", [
-    (4096, 64, 1e-8, "uniform", "fio", 0, dict(oversample=2.0, oversample_leaf=4.0)),   # config 1
+    (4096, 64, 1e-8, "uniform", "fio", 0, dict(oversample=2.0, oversample_leaf=4.0)),   # N = 4096, eps = 1e-8
     (2048, 16, 1e-6, "jitter", "dft", 0, {}),                                            # odd L
     (2048, 8, 1e-6, "uniform", "fio", 1, {}),                                            # Example 1
     (4096, 64, 1e-6, "schlomilch", "j0", 0, dict(oversample=2.0, oversample_leaf=4.0)),  # Example 2

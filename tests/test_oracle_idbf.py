@@ -73,7 +73,7 @@ def test_paper_example1_settings():
     assert e_15 < 1e-13
 
 
-def test_baseline_fio_config_small():
+def test_benchmark_fio_kernel_small():
     # the large-c' FIO (c = (2 + sin 2pi x sin 4pi x)/3), N = 4096, leaf 64, eps = 1e-8,
     # Mock-Chebyshev with 4x oversampling at the leaf step and 2x above it
     N, n0, eps = 4096, 64, 1e-8
