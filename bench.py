@@ -296,7 +296,7 @@ def gpu_arm(args, rank, world, local):
     tune = {}
     for name, mode in (("df64", P.MODE_DF64), ("fp32", P.MODE_FP32)):
         if name in want:
-            ms_sum = plan.autotune(mode, reps=3)
+            ms_sum = plan.autotune(mode, reps=10)  # short levels run for ~30 us: enough launches to rank them
             fmt = P.STORE_DF64 if name == "df64" else P.STORE_C64
             tune[name] = {"level_variants": plan.stats()["level_variant"][fmt], "sum_of_level_ms": ms_sum}
 
