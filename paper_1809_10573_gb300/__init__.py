@@ -14,12 +14,12 @@ import torch
 
 from . import _lib
 from ._lib import (KERNEL_DFT, KERNEL_FIO1D, KERNEL_J0, MODE_DF64, MODE_FP32, MODE_FP64, MODE_TF32X3,
-                   SAMPLE_ALL, SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, STORE_C64, STORE_C128,
+                   NUM_FWD_VARIANTS, SAMPLE_ALL, SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, STORE_C64, STORE_C128,
                    STORE_DF64, IDBFError)
 
 __all__ = ["Plan", "Batch", "IDBFError", "apply", "IDBFApply", "kernel_matvec_rows", "KERNEL_FIO1D", "KERNEL_DFT", "KERNEL_J0", "MODE_FP64",
            "MODE_DF64", "MODE_FP32", "MODE_TF32X3", "STORE_C128", "STORE_DF64", "STORE_C64",
-           "SAMPLE_MOCK_CHEBYSHEV", "SAMPLE_RANDOM", "SAMPLE_ALL"]
+           "SAMPLE_MOCK_CHEBYSHEV", "SAMPLE_RANDOM", "SAMPLE_ALL", "NUM_FWD_VARIANTS"]
 
 _VEC_DTYPE = {MODE_FP64: torch.complex128, MODE_DF64: torch.complex128,
               MODE_FP32: torch.complex64, MODE_TF32X3: torch.complex64}

@@ -205,6 +205,10 @@ constexpr int TCW = 6;                   // warps per consumer team
 constexpr int TCT = TCW * 32;            // threads per team (one output row each)
 constexpr int MAX_RPT = 2;               // output rows per team thread: rows <= MAX_RPT * TCT
 constexpr int FLUSH_TERMS = 16;          // double-float partial sums are folded after >= 16 terms
+// A block with rows <= TCT / 2 would leave most of a team idle: its columns are then split
+// between up to MAX_GROUPS groups of `rows` threads (group g takes columns g, g + G, ... of every
+// chunk), and the groups' partial sums are folded in the epilogue.
+constexpr int MAX_GROUPS = 4;
 // Ring of stages and team layout per arithmetic. Chunk i (counted over the whole launch) goes to
 // stage i % STAGES and to team i % TEAMS, so with STAGES a multiple of TEAMS every stage is read
 // by one team only, and a team never waits for a phase of a stage more than one phase ahead of
@@ -284,9 +288,10 @@ struct Geo {
 };
 // Shared memory: the stage ring, two input buffers (node inputs, copied by the producer), two
 // index buffers (q and p lists of both blocks), the gathered operands, the row-ID accumulator t,
-// the team reduction buffer and the mbarriers.
+// the reduction buffer and the mbarriers. The reduction buffer holds one partial sum per thread of
+// teams 1.. (and, with the column split, of team 0 too).
 template <class P, class RG>
-__host__ __device__ inline Geo geometry(int max_in, int max_out, int max_cols_pair, int rpt) {
+__host__ __device__ inline Geo geometry(int max_in, int max_out, int max_cols_pair, int rpt, int split) {
   using V = typename P::vec_t;
   using G = typename P::gv_t;
   constexpr int STAGES = RG::STAGES, STAGE_BYTES = RG::STAGE_BYTES;
@@ -301,13 +306,14 @@ __host__ __device__ inline Geo geometry(int max_in, int max_out, int max_cols_pa
   q.g_off = q.ibuf_off + ((2 * (size_t)q.icap * sizeof(int32_t) + 127) & ~(size_t)127);
   q.t_off = q.g_off + (((size_t)gsz * sizeof(G) + 127) & ~(size_t)127);
   q.red_off = q.t_off + (((size_t)max_out * sizeof(V) + 127) & ~(size_t)127);
-  q.bar_off = q.red_off + (((size_t)(RG::TEAMS > 1 ? RG::TEAMS - 1 : 1) * rpt * TCT * sizeof(typename P::part_t) + 127) & ~(size_t)127);
+  const int slots = split ? RG::TEAMS : (RG::TEAMS > 1 ? RG::TEAMS - 1 : 1);
+  q.bar_off = q.red_off + (((size_t)slots * rpt * TCT * sizeof(typename P::part_t) + 127) & ~(size_t)127);
   q.total = q.bar_off + 4 * STAGES * sizeof(uint64_t);
   return q;
 }
 }  // namespace strm
 
-template <class P, class RG, int RPT>
+template <class P, class RG, int RPT, bool SPLIT>
 __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     k_level_stream(DevLevel d, const typename P::mat_t* __restrict__ mat, IO<typename P::vec_t> io, int max_in,
                    int max_out, int max_cols_pair, int x_bulk, int* __restrict__ status, uint64_t limit_ns,
@@ -321,7 +327,8 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
   constexpr int STAGES = RG::STAGES, STAGE_BYTES = RG::STAGE_BYTES;
   constexpr int TEAMS = RG::TEAMS, NCT = RG::NCT;
   extern __shared__ __align__(128) unsigned char smem[];
-  const Geo geo = geometry<P, RG>(max_in, max_out, max_cols_pair, RPT);
+  static_assert(RPT == 1 || !SPLIT, "the column split is for one output row per thread");
+  const Geo geo = geometry<P, RG>(max_in, max_out, max_cols_pair, RPT, SPLIT);
   unsigned char* stages = smem;
   V* ubuf = (V*)(smem + geo.vec_off);              // [2][ucap]
   int32_t* ibuf = (int32_t*)(smem + geo.ibuf_off);  // [2][icap]
@@ -537,6 +544,10 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
 #pragma unroll
       for (int k = 0; k < RPT; ++k) P::init(acc[k]);
       const bool work = rows > 0 && cols > 0;
+      // column split of short blocks: this thread takes row rr of the block in column group grp
+      const int ngrp = (SPLIT && rows > 0) ? min(MAX_GROUPS, max(1, TCT / rows)) : 1;
+      const int grp = ngrp > 1 ? tr / rows : 0;
+      const int rr = tr - grp * rows;
       if (work) {
         const int cpc = cols_per_chunk(rows, ES, STAGE_BYTES);
         const uintptr_t base = (uintptr_t)(mat + mov[c]);
@@ -552,7 +563,13 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
             const int shift = ES == 16 ? 0 : (int)((src & 15) / ES);  // 16-byte entries are never shifted
             const M* st = (const M*)(stages + (size_t)stg * STAGE_BYTES) + shift + tr;
             if (RPT == 1) {
-              if (tr < rows) {
+              if (ngrp > 1) {
+                if (grp < ngrp) {
+                  const M* sg = st - tr + rr;
+#pragma unroll 4
+                  for (int jj = grp; jj < nc; jj += ngrp) P::mac(acc[0], sg[jj * rows], gc[j0 + jj]);
+                }
+              } else if (tr < rows) {
 #pragma unroll 4
                 for (int jj = 0; jj < nc; ++jj) P::mac(acc[0], st[jj * rows], gc[j0 + jj]);
               }
@@ -577,11 +594,15 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
         }
 #pragma unroll
         for (int k = 0; k < RPT; ++k) P::flush(acc[k]);
-        // teams 1.. hand their partial sums to team 0
-        if (team > 0) {
+        // teams 1.. hand their partial sums to team 0; with the column split, team 0's groups
+        // 1.. too (slot team * TCT + tr; without it, slot (team - 1) * RPT * TCT + tr)
+        if (ngrp > 1) {
+          if ((team > 0 || grp > 0) && grp < ngrp) red[team * TCT + tr] = P::part(acc[0]);
+        } else if (team > 0) {
+          const int slot = SPLIT ? team : team - 1;
 #pragma unroll
           for (int k = 0; k < RPT; ++k)
-            if (tr + k * TCT < rows) red[((team - 1) * RPT + k) * TCT + tr] = P::part(acc[k]);
+            if (tr + k * TCT < rows) red[(slot * RPT + k) * TCT + tr] = P::part(acc[k]);
         }
       }
       consumer_sync<NCT>();
@@ -592,7 +613,13 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
         for (int k = 0; k < RPT; ++k) {
           const int r = tr + k * TCT;
           if (r >= rows) continue;
-          for (int tm = 1; tm < TEAMS; ++tm) P::combine(acc[k], red[((tm - 1) * RPT + k) * TCT + tr]);
+          if (ngrp > 1) {
+            for (int tm = 0; tm < TEAMS; ++tm)
+              for (int gq = tm == 0 ? 1 : 0; gq < ngrp; ++gq) P::combine(acc[0], red[tm * TCT + gq * rows + tr]);
+          } else {
+            for (int tm = 1; tm < TEAMS; ++tm)
+              P::combine(acc[k], red[((SPLIT ? tm : tm - 1) * RPT + k) * TCT + tr]);
+          }
           const V v = P::fin(acc[k]);
           if (d.kind == KIND_U) {
             V* q = &t[ix[(c ? l1 : l0) + r]];
@@ -648,22 +675,31 @@ __global__ void __launch_bounds__(kWarpNodeWarps * 32) k_level_warp(DevLevel d, 
 // Forward level kernels for one right-hand side. Variant 0: the per-node kernel; variants
 // 1..6: the streaming kernel with ring layout A, B or C (see strm::Ring*), each with the node
 // inputs copied by the producer (odd variants) or loaded by the consumers (even variants);
-// variant 7: the warp-per-node kernel (levels whose blocks have at most 128 rows).
-constexpr int kNumFwdVariants = 8;
+// variant 7: the warp-per-node kernel (levels whose blocks have at most 128 rows); variants
+// 8..13: variants 1..6 with the column split of blocks of at most 96 rows (strm::MAX_GROUPS).
+constexpr int kNumFwdVariants = IDBF_NUM_FWD_VARIANTS;
 
 static int default_variant(int fmt) { return fmt == IDBF_STORE_C128 ? 0 : 1; }
 
 template <class P, class RG>
-static idbf_status launch_stream(Plan* p, int l, bool bulk, const void* x, IO<typename P::vec_t> io, cudaStream_t st) {
+static idbf_status launch_stream(Plan* p, int l, bool bulk, bool split_short, const void* x, IO<typename P::vec_t> io,
+                                 cudaStream_t st) {
   using V = typename P::vec_t;
   const LevelInfo& li = p->lv[l];
   if (!p->d_status || li.max_rows > strm::MAX_RPT * strm::TCT ||
       li.max_rows * (int)sizeof(typename P::mat_t) > RG::STAGE_BYTES - 32)
     return IDBF_EUNSUPPORTED;
   const int rpt = li.max_rows <= strm::TCT ? 1 : 2;
-  const strm::Geo geo = strm::geometry<P, RG>(li.max_in, li.max_out, li.max_cols_pair, rpt);
   // per-SM shared memory 228 KB: each CTA also reserves 1 KB and 128 B of static storage
-  if (geo.total > (size_t)(RG::CTAS == 1 ? 226 * 1024 : 112 * 1024)) return IDBF_EUNSUPPORTED;
+  const size_t cap = (size_t)(RG::CTAS == 1 ? 226 * 1024 : 112 * 1024);
+  // the column split of short blocks (one output row per thread only) if its buffer fits
+  int split = rpt == 1 && split_short ? 1 : 0;
+  strm::Geo geo = strm::geometry<P, RG>(li.max_in, li.max_out, li.max_cols_pair, rpt, split);
+  if (split && geo.total > cap) {
+    split = 0;
+    geo = strm::geometry<P, RG>(li.max_in, li.max_out, li.max_cols_pair, rpt, split);
+  }
+  if (geo.total > cap) return IDBF_EUNSUPPORTED;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -672,17 +708,16 @@ static idbf_status launch_stream(Plan* p, int l, bool bulk, const void* x, IO<ty
   const int use_bulk = bulk && (l > 0 || x_ok);
   const DevLevel d = p->level(l);
   const typename P::mat_t* mat = (const typename P::mat_t*)p->lmat[fmt_of<P>()][l];
-  if (rpt == 1) {
-    IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_stream<P, RG, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
-    k_level_stream<P, RG, 1><<<ctas, RG::NTHREADS, geo.total, st>>>(d, mat, io, li.max_in, li.max_out, li.max_cols_pair,
-                                                                    use_bulk, p->d_status, p->wait_limit_ns,
-                                                                    p->producer_enabled);
-  } else {
-    IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_stream<P, RG, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
-    k_level_stream<P, RG, 2><<<ctas, RG::NTHREADS, geo.total, st>>>(d, mat, io, li.max_in, li.max_out, li.max_cols_pair,
-                                                                    use_bulk, p->d_status, p->wait_limit_ns,
-                                                                    p->producer_enabled);
-  }
+  auto go = [&](auto kern) -> idbf_status {
+    IDBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
+    kern<<<ctas, RG::NTHREADS, geo.total, st>>>(d, mat, io, li.max_in, li.max_out, li.max_cols_pair, use_bulk,
+                                                p->d_status, p->wait_limit_ns, p->producer_enabled);
+    return IDBF_OK;
+  };
+  idbf_status s = rpt == 2 ? go(k_level_stream<P, RG, 2, false>)
+                  : split  ? go(k_level_stream<P, RG, 1, true>)
+                           : go(k_level_stream<P, RG, 1, false>);
+  if (s != IDBF_OK) return s;
   IDBF_CUDA_TRY(cudaGetLastError());
   return IDBF_OK;
 }
@@ -717,13 +752,14 @@ static idbf_status launch_fwd_variant(Plan* p, int l, int v, const void* x, void
   io.win = win; io.wout = wout;
   if (v == 7) return launch_warp_node<P>(p, l, io, st, fmt);
   if (v != 0 && fmt == IDBF_STORE_C128) return IDBF_EUNSUPPORTED;  // FP64: per-node or warp-per-node kernel
-  switch (v) {
-    case 1: return launch_stream<P, strm::RingA>(p, l, true, x, io, st);
-    case 2: return launch_stream<P, strm::RingA>(p, l, false, x, io, st);
-    case 3: return launch_stream<P, strm::RingB>(p, l, true, x, io, st);
-    case 4: return launch_stream<P, strm::RingB>(p, l, false, x, io, st);
-    case 5: return launch_stream<P, strm::RingC>(p, l, true, x, io, st);
-    case 6: return launch_stream<P, strm::RingC>(p, l, false, x, io, st);
+  const bool split = v >= 8;
+  switch (split ? v - 7 : v) {
+    case 1: return launch_stream<P, strm::RingA>(p, l, true, split, x, io, st);
+    case 2: return launch_stream<P, strm::RingA>(p, l, false, split, x, io, st);
+    case 3: return launch_stream<P, strm::RingB>(p, l, true, split, x, io, st);
+    case 4: return launch_stream<P, strm::RingB>(p, l, false, split, x, io, st);
+    case 5: return launch_stream<P, strm::RingC>(p, l, true, split, x, io, st);
+    case 6: return launch_stream<P, strm::RingC>(p, l, false, split, x, io, st);
     default: break;
   }
   const LevelInfo& li = p->lv[l];

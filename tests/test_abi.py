@@ -85,3 +85,13 @@ def test_null_arguments(lib):
     assert lib.idbf_apply(None, None, None, 1, 1, 0, None) == _lib.EINVAL
     assert lib.idbf_stats(None, None) == _lib.EINVAL
     lib.idbf_destroy(None)
+
+
+def test_python_constants_match_the_header():
+    src = open(HEADER).read()
+    defs = dict(re.findall(r"#define (IDBF_[A-Z0-9_]+) (\d+)\b", src))
+    pairs = {"IDBF_NUM_FWD_VARIANTS": P.NUM_FWD_VARIANTS, "IDBF_MODE_TF32X3": P.MODE_TF32X3,
+             "IDBF_MODE_FP32": P.MODE_FP32, "IDBF_STORE_C64": P.STORE_C64, "IDBF_KERNEL_J0": P.KERNEL_J0,
+             "IDBF_SAMPLE_ALL": P.SAMPLE_ALL}
+    for name, val in pairs.items():
+        assert int(defs[name]) == val, name

@@ -168,7 +168,7 @@ def test_every_forward_variant_matches_oracle(case, mode, fmt, tol):
     dt = torch.complex64 if mode == P.MODE_FP32 else torch.complex128
     xd = torch.from_numpy(X).to(dt).cuda()
     ref = idbf.apply(c["F"], X)
-    for v in range(8):   # FP64 runs variants 0 and 7; the streaming ones fall back to 0
+    for v in range(P.NUM_FWD_VARIANTS):   # FP64 runs variants 0 and 7; the streaming ones fall back to 0
         plan.set_level_variants(mode, [v] * (c["F"].L + 1))
         y = plan.apply(xd, mode=mode)
         plan.sync_status()
@@ -176,5 +176,5 @@ def test_every_forward_variant_matches_oracle(case, mode, fmt, tol):
     ms = plan.autotune(mode, reps=2)
     assert ms > 0
     chosen = plan.stats()["level_variant"][fmt]
-    assert all(0 <= v < 8 for v in chosen)
+    assert all(0 <= v < P.NUM_FWD_VARIANTS for v in chosen)
     assert rel(plan.apply(xd, mode=mode).cpu().numpy(), ref) < tol

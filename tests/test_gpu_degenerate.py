@@ -69,7 +69,7 @@ def test_every_variant_and_the_batch_on_degenerate_blocks(tiny, mode, fmt, dt, t
     X = inputs.complex_gaussian(N, 1, seed=7)
     ref = idbf.apply(tiny["F"], X)
     xd = torch.from_numpy(X.astype(dt)).cuda()
-    for v in range(8):
+    for v in range(P.NUM_FWD_VARIANTS):
         plan.set_level_variants(mode, [v] * 3)
         assert rel(plan.apply(xd, mode=mode).cpu().numpy(), ref) < tol, f"variant {v}"
         plan.sync_status()
