@@ -282,6 +282,15 @@ __host__ __device__ __forceinline__ int cols_per_chunk(int rows, int es, int sta
   return max(1, cap / max(rows, 1));
 }
 
+// A node's description: input segment (offset, lengths), index-list and block offsets, block
+// shapes, and where the outputs go. The producer loads it one node ahead and publishes it in
+// shared memory before its arrival on the node's input barrier, so that the consumers start a
+// node without a global-memory round trip.
+struct NodeMeta {
+  int64_t in0, io[2], mo[2], ob[2];
+  int l0, l1, rows[2], cols[2], olen0;
+};
+
 struct Geo {
   size_t vec_off, ibuf_off, g_off, t_off, red_off, bar_off, total;
   int ucap, icap;  // elements of one input buffer, ints of one index buffer
@@ -343,6 +352,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
   // consumer barrier and read after it, so that all consumer warps leave the loop together.
   __shared__ int abort_flag;
   __shared__ int cons_abort;
+  __shared__ NodeMeta nmeta[2];  // description of the node in input buffer b
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
@@ -366,12 +376,8 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     uint32_t it = 0, nn = 0;
     bool ok = true;
     // node descriptions are loaded one node ahead, so that no copy waits for them
-    struct Meta {
-      int64_t in0, io[2], mo[2];
-      int l0, l1, rows[2], cols[2];
-    };
     auto meta = [&](int64_t jj) {
-      Meta m;
+      NodeMeta m;
       m.in0 = d.lev == 0 ? 0 : d.in_off[2 * jj];
       m.l0 = d.lev == 0 ? d.n0 : d.in_len[2 * jj];
       m.l1 = d.lev == 0 ? 0 : d.in_len[2 * jj + 1];
@@ -382,11 +388,19 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
         m.rows[c] = d.rows[2 * jj + c];
         m.cols[c] = d.cols[2 * jj + c];
       }
+      m.ob[0] = m.ob[1] = 0;
+      m.olen0 = 0;
+      if (d.lev < d.L) {
+        const int64_t s0 = out_seg_id(d, jj, 0), s1 = out_seg_id(d, jj, 1);
+        m.ob[0] = d.out_off[s0];
+        m.ob[1] = d.out_off[s1];
+        m.olen0 = d.out_len[s0];
+      }
       return m;
     };
-    Meta nxt = meta(blockIdx.x < d.m ? (int64_t)blockIdx.x : 0);
+    NodeMeta nxt = meta(blockIdx.x < d.m ? (int64_t)blockIdx.x : 0);
     for (int64_t j = blockIdx.x; j < d.m && ok; j += gridDim.x, ++nn) {
-      const Meta cur = nxt;
+      const NodeMeta cur = nxt;
       if (j + gridDim.x < d.m) nxt = meta(j + gridDim.x);
       // node inputs and index lists into buffer nn & 1 (released by the consumers of node nn-2)
       const int b = nn & 1;
@@ -412,6 +426,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
           icopy[c] = (uint32_t)((((uintptr_t)is + ib + 15) & ~(uintptr_t)15) - (uintptr_t)ia[c]);
         }
       }
+      nmeta[b] = cur;  // visible to the consumers through the release of the arrival below
       if (producer_enabled) {
         mbar_expect_tx(&in_full[b], ucopy + icopy[0] + icopy[1]);
         if (ucopy) bulk_g2s(ubuf + (size_t)b * geo.ucap, ua, ucopy, &in_full[b]);
@@ -466,25 +481,18 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     consumer_sync<NCT>();
     if (*(volatile int*)&cons_abort) break;
     const int b = nn & 1;
-    int l0, l1;
-    if (d.lev == 0) { l0 = d.n0; l1 = 0; }
-    else { l0 = d.in_len[2 * j]; l1 = d.in_len[2 * j + 1]; }
-    const int rows0 = d.rows[2 * j], rows1 = d.rows[2 * j + 1];
-    const int cols0 = d.cols[2 * j], cols1 = d.cols[2 * j + 1];
-    // where the node's outputs go, loaded now so that the epilogues after the barriers below do
-    // not wait for them
-    int64_t obv[2] = {0, 0};
-    int olen0 = 0;
-    const int64_t in0 = d.lev == 0 ? 0 : d.in_off[2 * j];
-    const int64_t iov[2] = {d.kind != KIND_S ? d.ioff[2 * j] : 0, d.kind != KIND_S ? d.ioff[2 * j + 1] : 0};
-    const int64_t mov[2] = {d.moff[2 * j], d.moff[2 * j + 1]};
-    if (d.lev < d.L) {
-      const int64_t s0 = out_seg_id(d, j, 0), s1 = out_seg_id(d, j, 1);
-      obv[0] = d.out_off[s0];
-      obv[1] = d.out_off[s1];
-      olen0 = d.out_len[s0];
-    }
     if (!failed && !wait_bounded(&in_full[b], (nn >> 1) & 1, limit_ns, &abort_flag)) failed = true;
+    // the node's description from the producer (acquired by the wait above); after a failed wait
+    // it may be incomplete, so every size is zero and the loops below do nothing
+    const NodeMeta& nm = nmeta[b];
+    const int l0 = failed ? 0 : nm.l0, l1 = failed ? 0 : nm.l1;
+    const int rows0 = failed ? 0 : nm.rows[0], rows1 = failed ? 0 : nm.rows[1];
+    const int cols0 = failed ? 0 : nm.cols[0], cols1 = failed ? 0 : nm.cols[1];
+    const int64_t obv[2] = {nm.ob[0], nm.ob[1]};
+    const int olen0 = failed ? 0 : nm.olen0;
+    const int64_t in0 = nm.in0;
+    const int64_t iov[2] = {d.kind != KIND_S ? nm.io[0] : 0, d.kind != KIND_S ? nm.io[1] : 0};
+    const int64_t mov[2] = {nm.mo[0], nm.mo[1]};
     // inputs (shifted within 16 bytes of the copy) and index lists in shared memory
     const V* u;
     {
