@@ -72,6 +72,16 @@ def fp32_fma_peak():
     return sms * 128 * mhz * 1e6 / 1e12, f"{sms} SMs x 128 FP32 FMA/clk x {mhz:.0f} MHz"
 
 
+def parse_level_variants(spec):
+    """'df64=7,1,10;fp32=7,3,1' -> {'df64': [7, 1, 10], 'fp32': [7, 3, 1]}."""
+    out = {}
+    for part in (spec or "").split(";"):
+        if part.strip():
+            name, vals = part.split("=", 1)
+            out[name.strip()] = [int(v) for v in vals.split(",")]
+    return out
+
+
 def read_traffic_summary():
     """DRAM bytes per algorithmic byte of the level kernel from the committed ncu summary, valid
     only while the kernel source is the one that was profiled."""
@@ -292,12 +302,20 @@ def gpu_arm(args, rank, world, local):
     rel_32 = float(torch.linalg.norm(y32.to(torch.complex128) - y64) / nrm) if "fp32" in want else None
     plan.set_storage(*fmts_final)
 
-    # autotuner: fastest forward kernel per level for each timed mode (untimed)
+    # autotuner: fastest forward kernel per level for each timed mode (untimed), unless the
+    # variants are given (e.g. to profile exactly the choices of an earlier uninstrumented run)
     tune = {}
+    fixed = parse_level_variants(args.level_variants)
     for name, mode in (("df64", P.MODE_DF64), ("fp32", P.MODE_FP32)):
         if name in want:
-            ms_sum = plan.autotune(mode, reps=10)  # short levels run for ~30 us: enough launches to rank them
             fmt = P.STORE_DF64 if name == "df64" else P.STORE_C64
+            if name in fixed:
+                if len(fixed[name]) != L + 1:
+                    raise SystemExit(f"--level-variants {name}: {L + 1} values expected")
+                plan.set_level_variants(mode, fixed[name])
+                tune[name] = {"level_variants": plan.stats()["level_variant"][fmt], "given": True}
+                continue
+            ms_sum = plan.autotune(mode, reps=10)  # short levels run for ~30 us: enough launches to rank them
             tune[name] = {"level_variants": plan.stats()["level_variant"][fmt], "sum_of_level_ms": ms_sum}
 
     def timed(mode, vec, steps, warmup, sampler_index=None):
@@ -602,6 +620,9 @@ def main():
                     help="N = 2^log2n (default: the benchmarked size of the workload, 20 for apply and "
                          "autograd, 18 for mrhs; smaller cases for profiling)")
     ap.add_argument("--modes", default="df64,fp64,fp32", help="apply modes to time (df64 is the headline)")
+    ap.add_argument("--level-variants", default=None,
+                    help="per-level forward variants instead of the autotuner, e.g. 'df64=7,1,10,...;fp32=...' "
+                         "(apply workload)")
     ap.add_argument("--workload", choices=["apply", "mrhs", "batch", "autograd"], default="apply",
                     help="apply: the headline single-vector apply at N=2^20; the others print their own lines")
     args = ap.parse_args()
