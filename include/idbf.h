@@ -194,7 +194,9 @@ idbf_status idbf_apply_noalloc(idbf_plan plan, const void* x, void* y, int64_t n
  * with three shared-memory ring layouts, node inputs copied by the producer warp or loaded by
  * the consumers; 7: one warp per node, for levels of short blocks; 8-13: 1-6 with the columns
  * of blocks of at most 96 rows split between up to four thread groups, whose partial sums are
- * added at the end) `reps` times with CUDA events on `stream`, and keep the fastest per level in the
+ * added at the end; 14-15: a fourth ring layout with four CTAs per SM and small stages, for
+ * levels of short blocks, with the split) `reps` times with CUDA events on `stream`, and keep
+ * the fastest per level in the
  * plan (idbf_stats reports them). Later idbf_apply calls use the choices; results are identical
  * up to the summation order of the double-float / FP32 partial sums. Synchronous; allocates two
  * N-vector temporaries. *apply_ms (if not NULL) receives the summed best level times.
@@ -204,7 +206,7 @@ idbf_status idbf_autotune(idbf_plan plan, int32_t mode, int32_t reps, void* stre
 /* idbf_set_level_variants - set the forward kernel variant of every level for `mode` directly
  * (n = L + 1 values in 0..IDBF_NUM_FWD_VARIANTS-1, -1 = default; n = 0 clears), e.g. to restore the choices of an
  * earlier idbf_autotune. A variant that does not fit a level falls back to variant 0. */
-#define IDBF_NUM_FWD_VARIANTS 14
+#define IDBF_NUM_FWD_VARIANTS 16
 idbf_status idbf_set_level_variants(idbf_plan plan, int32_t mode, const int32_t* variants, int32_t n);
 
 /* idbf_set_tc_split - operand splitting of the 3xTF32 tensor-core mode: 0 = x_hi + x_lo with

@@ -227,8 +227,12 @@ struct RingC {  // one CTA per SM, four teams, eight stages
   static constexpr int TEAMS = 4, STAGES = 8, STAGE_BYTES = 22 * 1024, CTAS = 1;
   static constexpr int NCT = TEAMS * TCT, NTHREADS = NCT + 32;
 };
+struct RingD {  // four CTAs per SM, one team each, small stages: levels of short blocks
+  static constexpr int TEAMS = 1, STAGES = 3, STAGE_BYTES = 12 * 1024, CTAS = 4;
+  static constexpr int NCT = TEAMS * TCT, NTHREADS = NCT + 32;
+};
 static_assert(RingA::STAGES % RingA::TEAMS == 0 && RingB::STAGES % RingB::TEAMS == 0 &&
-                  RingC::STAGES % RingC::TEAMS == 0,
+                  RingC::STAGES % RingC::TEAMS == 0 && RingD::STAGES % RingD::TEAMS == 0,
               "every stage must belong to one team");
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -684,7 +688,9 @@ __global__ void __launch_bounds__(kWarpNodeWarps * 32) k_level_warp(DevLevel d, 
 // 1..6: the streaming kernel with ring layout A, B or C (see strm::Ring*), each with the node
 // inputs copied by the producer (odd variants) or loaded by the consumers (even variants);
 // variant 7: the warp-per-node kernel (levels whose blocks have at most 128 rows); variants
-// 8..13: variants 1..6 with the column split of blocks of at most 96 rows (strm::MAX_GROUPS).
+// 8..13: variants 1..6 with the column split of blocks of at most 96 rows (strm::MAX_GROUPS);
+// variants 14, 15: ring layout D (four CTAs per SM) with the column split, inputs copied by the
+// producer or loaded by the consumers.
 constexpr int kNumFwdVariants = IDBF_NUM_FWD_VARIANTS;
 
 static int default_variant(int fmt) { return fmt == IDBF_STORE_C128 ? 0 : 1; }
@@ -698,8 +704,8 @@ static idbf_status launch_stream(Plan* p, int l, bool bulk, bool split_short, co
       li.max_rows * (int)sizeof(typename P::mat_t) > RG::STAGE_BYTES - 32)
     return IDBF_EUNSUPPORTED;
   const int rpt = li.max_rows <= strm::TCT ? 1 : 2;
-  // per-SM shared memory 228 KB: each CTA also reserves 1 KB and 128 B of static storage
-  const size_t cap = (size_t)(RG::CTAS == 1 ? 226 * 1024 : 112 * 1024);
+  // per-SM shared memory 228 KB: each CTA also reserves 1 KB and < 1 KB of static storage
+  const size_t cap = (size_t)(228 / RG::CTAS - 2) * 1024;
   // the column split of short blocks (one output row per thread only) if its buffer fits
   int split = rpt == 1 && split_short ? 1 : 0;
   strm::Geo geo = strm::geometry<P, RG>(li.max_in, li.max_out, li.max_cols_pair, rpt, split);
@@ -760,6 +766,7 @@ static idbf_status launch_fwd_variant(Plan* p, int l, int v, const void* x, void
   io.win = win; io.wout = wout;
   if (v == 7) return launch_warp_node<P>(p, l, io, st, fmt);
   if (v != 0 && fmt == IDBF_STORE_C128) return IDBF_EUNSUPPORTED;  // FP64: per-node or warp-per-node kernel
+  if (v == 14 || v == 15) return launch_stream<P, strm::RingD>(p, l, v == 14, true, x, io, st);
   const bool split = v >= 8;
   switch (split ? v - 7 : v) {
     case 1: return launch_stream<P, strm::RingA>(p, l, true, split, x, io, st);
