@@ -62,3 +62,11 @@ def test_clock_summary_parsing(tmp_path):
 def test_traffic_summary_requires_the_profiled_source(tmp_path, monkeypatch):
     v = bench.read_traffic_summary()
     assert v is None or v > 0
+
+
+def test_level_variants_option_parsing():
+    assert bench.parse_level_variants(None) == {}
+    assert bench.parse_level_variants("df64=14,1,10") == {"df64": [14, 1, 10]}
+    assert bench.parse_level_variants(" df64=7,1 ; fp32=3,15 ;") == {"df64": [7, 1], "fp32": [3, 15]}
+    with pytest.raises(ValueError):
+        bench.parse_level_variants("df64=7,x")
