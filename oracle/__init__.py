@@ -11,9 +11,12 @@ Factorization" (arXiv:1809.10573):
   interp.py   - the (eps, k) column and row IDs via a rank-revealing QR (Sec. 2.1, Lemma 2.1)
   idbf.py     - LRCS / MSCS / recursive MSCS construction (Sec. 2.2-2.4), the apply of
                 K ~ U^L ... U^h S^h V^h ... V^L (Eq. 1), its adjoint, and the dense matvec
-                and sampled relative error used in Sec. 3.
+                and sampled relative error used in Sec. 3; on uniform trees (Sec. 2) or on
+                coordinate-based dyadic trees with uneven leaves (Sec. 1, Example 3).
 
 Parity pins: every function is checked by tests/test_oracle_*.py against closed forms (DFT),
-exact low-rank reconstruction, LAPACK, SVD ranks and brute force on small inputs.
+exact low-rank reconstruction, LAPACK, SVD ranks and brute force on small inputs; the uneven
+leaves against an exact rational count, bitwise agreement with the uniform layout on uniform
+points, exact reconstruction with empty leaves, and the dense sum of Example 3.
 Parity unpinned: none of the functions above.
 """

@@ -1,21 +1,26 @@
 """IDBF construction and apply (oracle; test infrastructure only).
 
 Notation (Sec. 2): N = n0 2^L points, m = 2^L leaves, dyadic trees T_X (rows) and T_Omega
-(columns) with the root at depth 0 and the leaves at depth L. A row node at depth d and a
-column node at depth L + 1 - d form a complementary pair (Sec. 1); every ID below belongs to
-one such pair. h_V = floor(L/2) column-ID steps and h_U = L - h_V row-ID steps are taken
+(columns) with the root at depth 0 and the leaves at depth L. Leaf j of T_X holds the rows
+ro[j] .. ro[j+1]-1 and leaf j of T_Omega the columns co[j] .. co[j+1]-1; a node at depth d is
+the union of its 2^(L-d) leaves. Uniform trees (Sec. 2) have ro = co = 0, n0, 2 n0, .., N.
+Sec. 1 builds the trees by dyadic partitioning of the domains of X and Omega, so for points
+that are not uniformly spaced (Example 3) the leaves hold different numbers of points, some
+possibly none, and N need not be n0 2^L: dyadic_leaves() gives those offsets.
+A row node at depth d and a column node at depth L + 1 - d form a complementary pair (Sec. 1);
+every ID below belongs to one such pair. h_V = floor(L/2) column-ID steps and h_U = L - h_V row-ID steps are taken
 (Sec. 2.4 stops after L/2 steps for even L; odd L splits the steps unevenly).
 
 Construction, in the order of the LRCS (Sec. 2.2: row IDs first, then column IDs on the
 skeleton rows) repeated by recursive MSCS (Secs. 2.3-2.4), for s = 1 .. h_U:
   U step s, every (rho at depth L-s+1, kappa at depth s): row ID of K(rows, columns) with
-    rows    = the n0 rows of leaf rho (s = 1), else rhat(2rho, kappa/2) u rhat(2rho+1, kappa/2)
+    rows    = the rows of leaf rho (s = 1), else rhat(2rho, kappa/2) u rhat(2rho+1, kappa/2)
               (the merged leaves of the compressed tree, Sec. 2.2 and Fig. rc);
     columns = all columns of kappa (s = 1), else chat(tau, sigma) over the column nodes sigma
               at depth L-s+2 below kappa, tau the ancestor of rho at depth s-1;
     result  rhat(rho, kappa) and U(rho, kappa) = Lambda [I T]^T.
   V step s (s <= h_V), every (tau at depth s, sigma at depth L-s+1): column ID with
-    columns = the n0 columns of leaf sigma (s = 1), else chat(tau/2, 2sigma) u chat(tau/2, 2sigma+1);
+    columns = the columns of leaf sigma (s = 1), else chat(tau/2, 2sigma) u chat(tau/2, 2sigma+1);
     rows    = rhat(rho, kappa) over the row nodes rho at depth L-s+1 below tau, kappa the
               ancestor of sigma at depth s;
     result  chat(tau, sigma) and V(tau, sigma) = [I T] Lambda^*.
@@ -40,11 +45,16 @@ from . import interp, sampling
 
 
 class IDBF:
-    """Factors of K ~ U^L ... U^h S^h V^h ... V^L in the index form described above."""
+    """Factors of K ~ U^L ... U^h S^h V^h ... V^L in the index form described above.
 
-    def __init__(self, N, n0, L):
+    n0 is the leaf size of uniform trees and None for coordinate-based trees with uneven
+    leaves; ro and co are the row and column leaf offsets (m + 1 each) in both cases."""
+
+    def __init__(self, N, n0, L, ro=None, co=None):
         self.N, self.n0, self.L = N, n0, L
         self.m = 1 << L
+        self.ro = np.arange(0, N + 1, n0, dtype=np.int64) if ro is None else np.asarray(ro, np.int64)
+        self.co = np.arange(0, N + 1, n0, dtype=np.int64) if co is None else np.asarray(co, np.int64)
         self.hV = L // 2
         self.hU = L - self.hV
         self.U = {}     # (s, rho, kappa) -> (rows, IDResult)
@@ -66,6 +76,27 @@ def levels_of(N: int, n0: int) -> int:
     return L
 
 
+def dyadic_leaves(points, lo: float, hi: float, L: int):
+    """Leaf offsets of the dyadic tree of depth L over the domain [lo, hi) (Sec. 1): leaf j is
+    the interval [lo + (hi - lo) j / 2^L, lo + (hi - lo) (j + 1) / 2^L), and offset j is the
+    number of points below its left end. `points` must be ascending and inside [lo, hi)."""
+    p = np.asarray(points, dtype=np.float64)
+    if p.size and (p[0] < lo or p[-1] >= hi or np.any(np.diff(p) < 0)):
+        raise ValueError("points must be ascending and inside [lo, hi)")
+    edges = lo + (hi - lo) * (np.arange((1 << L) + 1, dtype=np.float64) / (1 << L))
+    off = np.searchsorted(p, edges, side="left").astype(np.int64)
+    off[-1] = p.size
+    return off
+
+
+def levels_for(N: int, n0: int) -> int:
+    """Tree depth for N points whose leaves should hold about n0 points: the L with N / 2^L
+    nearest to n0 on a log scale, at least 2 (the reading for N that is not n0 2^L)."""
+    if N <= 0 or n0 <= 0:
+        raise ValueError("N and n0 must be positive")
+    return max(2, int(round(math.log2(N / n0))))
+
+
 def _pick(coords, cands, ns, sampler, key):
     order = np.argsort(coords[cands], kind="stable")
     c = cands[order]
@@ -80,8 +111,8 @@ def _pick(coords, cands, ns, sampler, key):
     return c[sel]
 
 
-def build(kernel, x, xi, eps: float, n0: int, rank_cap: int = 0, t: float = 1,
-          sampler: str = "mock", seed: int = 0, t_leaf: float = None) -> IDBF:
+def build(kernel, x, xi, eps: float, n0, rank_cap: int = 0, t: float = 1,
+          sampler: str = "mock", seed: int = 0, t_leaf: float = None, leaves=None) -> IDBF:
     """Construct the IDBF of K(x_i, xi_j) by the recursive MSCS of Secs. 2.2-2.4.
 
     rank_cap = 0 takes k = min(#rows, #columns) of each complementary block (the k = min{m,n}
@@ -89,6 +120,8 @@ def build(kernel, x, xi, eps: float, n0: int, rank_cap: int = 0, t: float = 1,
     columns). sampler = "all" samples every candidate (no sampling; for exact-mode checks).
     t_leaf, when given, replaces t at the leaf step s = 1, where k = n0 is the full leaf size
     and an oscillatory kernel needs more samples than k to expose its row/column space.
+    leaves = (ro, co), the row and column leaf offsets of coordinate-based trees (see
+    dyadic_leaves), replaces the uniform leaves of size n0 (n0 is then ignored).
     """
     t_leaf = t if t_leaf is None else t_leaf
 
@@ -98,16 +131,31 @@ def build(kernel, x, xi, eps: float, n0: int, rank_cap: int = 0, t: float = 1,
     x = np.asarray(x, dtype=np.float64)
     xi = np.asarray(xi, dtype=np.float64)
     N = x.size
-    L = levels_of(N, n0)
-    F = IDBF(N, n0, L)
+    if xi.size != N:
+        raise ValueError("K must be square")
+    if leaves is None:
+        L = levels_of(N, n0)
+        F = IDBF(N, n0, L)
+    else:
+        ro, co = (np.asarray(a, dtype=np.int64) for a in leaves)
+        m = ro.size - 1
+        L = int(round(math.log2(max(m, 1))))
+        if co.size != ro.size or (1 << L) != m or L < 2:
+            raise ValueError("leaf offsets: 2^L + 1 entries each, L >= 2")
+        for o in (ro, co):
+            if o[0] != 0 or o[-1] != N or np.any(np.diff(o) < 0):
+                raise ValueError("leaf offsets must rise from 0 to N")
+        F = IDBF(N, None, L, ro, co)
+    ro, co = F.ro, F.co
     hV, hU = F.hV, F.hU
     for s in range(1, hU + 1):
         # U step s: row IDs for (rho at depth L-s+1, kappa at depth s)
         for rho in range(1 << (L - s + 1)):
             for kappa in range(1 << s):
                 if s == 1:
-                    rows = np.arange(rho * n0, (rho + 1) * n0)
-                    cands = np.arange(kappa * (N // 2), (kappa + 1) * (N // 2))
+                    rows = np.arange(ro[rho], ro[rho + 1])
+                    half = F.m >> 1
+                    cands = np.arange(co[kappa * half], co[(kappa + 1) * half])
                 else:
                     rows = np.concatenate([F.rhat[(s - 1, 2 * rho, kappa >> 1)],
                                            F.rhat[(s - 1, 2 * rho + 1, kappa >> 1)]])
@@ -128,7 +176,7 @@ def build(kernel, x, xi, eps: float, n0: int, rank_cap: int = 0, t: float = 1,
         for tau in range(1 << s):
             for sigma in range(1 << (L - s + 1)):
                 if s == 1:
-                    cols = np.arange(sigma * n0, (sigma + 1) * n0)
+                    cols = np.arange(co[sigma], co[sigma + 1])
                 else:
                     cols = np.concatenate([F.chat[(s - 1, tau >> 1, 2 * sigma)],
                                            F.chat[(s - 1, tau >> 1, 2 * sigma + 1)]])
@@ -159,11 +207,11 @@ def _as_block(x, N):
 
 def apply(F: IDBF, x):
     """y = U^L ... S ... V^L x (Eq. 1), level by level in natural loop order."""
-    N, n0, L, hV, hU = F.N, F.n0, F.L, F.hV, F.hU
+    N, L, hV, hU, ro, co = F.N, F.L, F.hV, F.hU, F.ro, F.co
     X = _as_block(x, N)
     z = {}
     for sigma in range(F.m):
-        xs = X[sigma * n0:(sigma + 1) * n0]
+        xs = X[co[sigma]:co[sigma + 1]]
         for tau in (0, 1):
             _, r = F.V[(1, tau, sigma)]
             z[(tau, sigma)] = xs[r.q] + r.T @ xs[r.p]
@@ -196,23 +244,23 @@ def apply(F: IDBF, x):
         w = wn
     Y = np.zeros_like(X)
     for rho in range(F.m):
-        t = np.zeros((n0, X.shape[1]), dtype=np.complex128)
+        t = np.zeros((ro[rho + 1] - ro[rho], X.shape[1]), dtype=np.complex128)
         for c in (0, 1):
             _, r = F.U[(1, rho, c)]
             wi = w[(rho, c)]
             t[r.q] += wi
             t[r.p] += r.T.T @ wi
-        Y[rho * n0:(rho + 1) * n0] = t
+        Y[ro[rho]:ro[rho + 1]] = t
     return Y.reshape(np.shape(x)) if np.ndim(x) == 1 else Y
 
 
 def apply_adjoint(F: IDBF, x):
     """y = (U^L ... S ... V^L)^* x: the factors in reverse order, each conjugate-transposed."""
-    N, n0, L, hV, hU = F.N, F.n0, F.L, F.hV, F.hU
+    N, L, hV, hU, ro, co = F.N, F.L, F.hV, F.hU, F.ro, F.co
     X = _as_block(x, N)
     w = {}
     for rho in range(F.m):
-        v = X[rho * n0:(rho + 1) * n0]
+        v = X[ro[rho]:ro[rho + 1]]
         for c in (0, 1):
             _, r = F.U[(1, rho, c)]
             w[(rho, c)] = v[r.q] + r.T.conj() @ v[r.p]
@@ -247,13 +295,13 @@ def apply_adjoint(F: IDBF, x):
         z = zn
     Y = np.zeros_like(X)
     for sigma in range(F.m):
-        u = np.zeros((n0, X.shape[1]), dtype=np.complex128)
+        u = np.zeros((co[sigma + 1] - co[sigma], X.shape[1]), dtype=np.complex128)
         for tau in (0, 1):
             _, r = F.V[(1, tau, sigma)]
             zi = z[(tau, sigma)]
             u[r.q] += zi
             u[r.p] += r.T.conj().T @ zi
-        Y[sigma * n0:(sigma + 1) * n0] = u
+        Y[co[sigma]:co[sigma + 1]] = u
     return Y.reshape(np.shape(x)) if np.ndim(x) == 1 else Y
 
 
@@ -285,7 +333,7 @@ def dense_factors(F: IDBF):
     IDBF approximation of K.
     """
     ex = export(F)
-    L, m, n0 = F.L, F.m, F.n0
+    L, m, ro, co = F.L, F.m, F.ro, F.co
     seg_len = ex["seg_len"]
     mats = []
     offs = [np.concatenate([[0], np.cumsum(seg_len[b])]) for b in range(L)]
@@ -296,13 +344,13 @@ def dense_factors(F: IDBF):
         H = 1 << (L - lev)
         for j in range(m):
             if lev == 0:
-                in_idx = np.arange(j * n0, (j + 1) * n0)
+                in_idx = np.arange(co[j], co[j + 1])
             else:
                 a, b = 2 * j, 2 * j + 1
                 in_idx = np.concatenate([np.arange(offs[lev - 1][a], offs[lev - 1][a + 1]),
                                          np.arange(offs[lev - 1][b], offs[lev - 1][b + 1])])
             if lev == L:
-                out_idx = [np.arange(j * n0, (j + 1) * n0)]
+                out_idx = [np.arange(ro[j], ro[j + 1])]
             else:
                 o = [(j // H) * 2 * H + (j % H) + c * H for c in (0, 1)]
                 out_idx = [np.arange(offs[lev][oc], offs[lev][oc + 1]) for oc in o]
@@ -344,9 +392,13 @@ def export(F: IDBF):
       kind 0: out_c = u[q_c] + M_c u[p_c], u = concat(in_0, in_1); M_c is |q_c| x |p_c|
       kind 1: out_c = M_c u
       kind 2: t[q_c] += in_c and t[p_c] += M_c in_c, t = concat(out_0, out_1); M_c = T_c^T
-    Matrices are row-major complex128; idx holds q_c then p_c (int32).
+    Matrices are row-major complex128; idx holds q_c then p_c (int32). Leaf j of x is
+    x[col_leaf_off[j] : col_leaf_off[j+1]] and leaf j of y is y[row_leaf_off[j] : row_leaf_off[j+1]];
+    n0 is 0 for uneven leaves (a layout the C interface, which takes leaves of n0 entries, does
+    not accept).
     """
-    L, m, n0, hV, hU = F.L, F.m, F.n0, F.hV, F.hU
+    L, m, hV, hU = F.L, F.m, F.hV, F.hU
+    n0 = F.n0 if F.n0 is not None else 0
     seg_len = np.zeros((L, 2 * m), dtype=np.int32)
     for b in range(L):
         if b < hV:
@@ -402,6 +454,7 @@ def export(F: IDBF):
                     _, r = F.U[(s, rho, 2 * kp + c)] if s > 1 else F.U[(1, j, c)]
                     put(lev, j, c, r.T.T, np.concatenate([r.q, r.p]))
     return dict(N=F.N, n0=n0, L=L, hV=hV, hU=hU, seg_len=seg_len, level_kind=kinds,
+                row_leaf_off=F.ro.copy(), col_leaf_off=F.co.copy(),
                 blk_rows=rows, blk_cols=cols, blk_moff=moff, blk_ioff=ioff,
                 mat=np.concatenate(mats) if mats else np.zeros(0, np.complex128),
                 idx=np.concatenate(idxs) if idxs else np.zeros(0, np.int32))

@@ -13,7 +13,9 @@ scipy.linalg.qr(pivoting=True); the triangular solve is scipy's solve_triangular
 Rank rule. Eq. (acc) reads k_eps = min{k : R_1(k,k) <= eps R_1(1,1)}, which would keep the
 first pivot that is already below the threshold. Reading adopted here: k_eps is the number of
 leading pivots with |R(j,j)| > eps |R(1,1)| (one fewer), capped by the rank parameter k and
-by min(|s|, n), and at least 1. A zero block gives k_eps = 1 and T = 0.
+by min(|s|, n), and at least 1. A zero block gives k_eps = 1 and T = 0. A block with no columns,
+or no sampled rows (an empty node of a coordinate-based tree, Sec. 1), gives k_eps = 0: no
+skeleton, every column redundant, T of size 0 x n.
 
 Row ID (end of Sec. 2.1): A ~ Lambda [I T]^* A_{q,:}. It is computed as the column ID of the
 transpose, A^T ~ (A^T)_{:,q} [I T] Lambda^T, i.e. A ~ Lambda [I T]^T A_{q,:}; the row
@@ -48,6 +50,9 @@ def column_id(As, eps: float, kcap: int) -> IDResult:
     """(eps, k)-cID of the sampled block As (|s| x n)."""
     As = np.asarray(As, dtype=np.complex128)
     ns, n = As.shape
+    if ns == 0 or n == 0:
+        return IDResult(np.zeros(0, np.int64), np.arange(n, dtype=np.int64),
+                        np.zeros((0, n), dtype=np.complex128), 0, np.zeros(0))
     R, P = sla.qr(As, mode="r", pivoting=True)
     d = np.abs(np.diag(R))
     kmax = min(ns, n, kcap if kcap > 0 else n)

@@ -8,7 +8,9 @@ Workloads follow the numerical examples of the paper (Sec. 3):
   * Example 1 (1D FIO): uniform grids x_i = i/N in [0,1) and xi_j = j - N/2 in [-N/2, N/2).
   * Example 3 (1D non-uniform DFT): the jittered variant below keeps the dyadic leaf
     structure of the uniform tree (each x_i stays inside its own cell) while moving every
-    point by a uniform offset of at most 0.3/N.
+    point by a uniform offset of at most 0.3/N; nufft_points draws the fully random points of
+    Example 3 (x uniform in [0,1), omega uniform in [-N/2, N/2)), whose coordinate-based
+    trees have leaves of uneven size.
 Right-hand sides are complex Gaussian: real and imaginary parts i.i.d. N(0, 1).
 """
 from __future__ import annotations
@@ -33,6 +35,15 @@ def jittered_grid(N: int, seed: int, jitter: float = 0.3):
     rng = np.random.default_rng(seed)
     i = np.arange(N, dtype=np.float64)
     return (i + rng.uniform(-jitter, jitter, N)) / N, i - N / 2
+
+
+def nufft_points(N: int, seed: int):
+    """Example 3: omega_k uniform in [-N/2, N/2) (the rows of K = exp(-2 pi i omega x)) and x_n
+    uniform in [0, 1) (its columns), N of each, both sorted ascending."""
+    rng = np.random.default_rng(seed)
+    omega = np.sort(rng.uniform(-N / 2, N / 2, N))
+    x = np.sort(rng.uniform(0.0, 1.0, N))
+    return omega, x
 
 
 def complex_gaussian(n: int, nrhs: int = 1, seed: int = 0, dtype=np.complex128):

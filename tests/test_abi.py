@@ -95,3 +95,16 @@ def test_python_constants_match_the_header():
              "IDBF_SAMPLE_ALL": P.SAMPLE_ALL}
     for name, val in pairs.items():
         assert int(defs[name]) == val, name
+
+
+def test_import_refuses_uneven_leaves(lib):
+    # factors on coordinate-based trees with uneven leaves (Example 3) are exported with n0 = 0:
+    # the C layout takes leaves of n0 entries, so the host-side validation refuses them
+    from oracle import idbf, kernels
+    from paper_1809_10573_gb300 import inputs
+    N = 96
+    om, xs = inputs.nufft_points(N, seed=4)
+    leaves = (idbf.dyadic_leaves(om, -N / 2, N / 2, 3), idbf.dyadic_leaves(xs, 0.0, 1.0, 3))
+    ex = idbf.export(idbf.build(kernels.Kernel(kernels.KIND_DFT, sign=-1), om, xs, 1e-6, None, leaves=leaves))
+    assert ex["n0"] == 0
+    assert _call_import(lib, ex)[0] == _lib.EINVAL
