@@ -6,7 +6,7 @@ with the CUDA path.
 
 It is a plain, slow restatement of Pang, Ho and Yang, "Interpolative Decomposition Butterfly
 Factorization" (arXiv:1809.10573):
-  kernels.py  - kernel entries K(x, xi) of the numerical examples (Sec. 3, Examples 1 and 3)
+  kernels.py  - kernel entries K(x, xi) of the numerical examples (Sec. 3, Examples 1-3)
   sampling.py - Mock-Chebyshev and uniform-random row/column sampling (Sec. 2.1)
   interp.py   - the (eps, k) column and row IDs via a rank-revealing QR (Sec. 2.1, Lemma 2.1)
   idbf.py     - LRCS / MSCS / recursive MSCS construction (Sec. 2.2-2.4), the apply of
