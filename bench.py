@@ -82,10 +82,20 @@ def parse_level_variants(spec):
     return out
 
 
+def code_digest(src: str) -> str:
+    """sha256 of C/CUDA source with its comments, trailing blanks and blank lines removed: an
+    edit of comments leaves the code, and so the profiled DRAM traffic, unchanged."""
+    import hashlib
+    import re
+    s = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    s = re.sub(r"//[^\n]*", "", s)
+    lines = [ln.rstrip() for ln in s.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()
+
+
 def read_traffic_summary():
     """DRAM bytes per algorithmic byte of the level kernel from the committed ncu summary, valid
-    only while the kernel source is the one that was profiled."""
-    import hashlib
+    only while the kernel's code is the one that was profiled (code_digest of apply.cu)."""
     path = os.path.join(ROOT, "profiles", "level_kernel_traffic.txt")
     try:
         kv = {}
@@ -93,8 +103,8 @@ def read_traffic_summary():
             if "=" in ln and not ln.startswith("#"):
                 k, v = ln.strip().split("=", 1)
                 kv[k.strip()] = v.strip()
-        src = open(os.path.join(ROOT, "paper_1809_10573_gb300", "csrc", "apply.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest() != kv.get("apply_cu_sha256"):
+        src = open(os.path.join(ROOT, "paper_1809_10573_gb300", "csrc", "apply.cu"), encoding="utf-8").read()
+        if code_digest(src) != kv.get("apply_cu_code_sha256"):
             return None
         return float(kv["dram_bytes_per_algorithmic_byte"])
     except Exception:

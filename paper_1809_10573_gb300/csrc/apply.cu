@@ -192,12 +192,14 @@ __global__ void __launch_bounds__(256) k_level_adj(DevLevel d, const typename P:
 }
 
 // ---------------------------------------------------------------------------------------------
-// Streaming forward level kernel (one right-hand side). Persistent CTAs (two per SM), each a
-// producer warp and NCW consumer warps. The producer copies every block of its nodes, a few
-// whole columns at a time, with cp.async.bulk into a ring of STAGES shared-memory stages
-// (mbarrier full / empty pairs); the consumers, one output row per thread, multiply the staged
-// columns with the gathered input held in shared memory. Each block is read from HBM once, in
-// large contiguous pieces, while the arithmetic runs from shared memory.
+// Streaming forward level kernel (one right-hand side). Persistent CTAs (one to four per SM,
+// by ring layout), each a producer warp and TEAMS consumer teams of TCW warps. The producer
+// copies every block of its nodes, a few whole columns at a time, with cp.async.bulk into a
+// ring of STAGES shared-memory stages (mbarrier full / empty pairs), and each node's inputs,
+// index lists and description into double buffers; the consumers, one output row per thread
+// (or per thread group, with the column split), multiply the staged columns with the gathered
+// input held in shared memory. Each block is read from HBM once, in large contiguous pieces,
+// while the arithmetic runs from shared memory.
 // Every wait is bounded (globaltimer): on a timeout the CTA sets bit 0 of *status, lets its
 // copies in flight land, and leaves; the host reads the status with idbf_sync_status.
 namespace strm {
@@ -213,8 +215,8 @@ constexpr int MAX_GROUPS = 4;
 // stage i % STAGES and to team i % TEAMS, so with STAGES a multiple of TEAMS every stage is read
 // by one team only, and a team never waits for a phase of a stage more than one phase ahead of
 // the last one it consumed there (an mbarrier parity wait cannot tell phase k from k + 2).
-//   double-float: issue bound, so one CTA per SM with four teams and large stages;
-//   FP32: memory-latency bound, two CTAs per SM with two teams each.
+// The autotuner picks the layout per level; on the FIO at N = 2^20 RingA takes the levels of
+// tall blocks and RingD most levels of short blocks, in double-float and in FP32 alike.
 struct RingA {  // two CTAs per SM, two teams each
   static constexpr int TEAMS = 2, STAGES = 4, STAGE_BYTES = 18 * 1024, CTAS = 2;
   static constexpr int NCT = TEAMS * TCT, NTHREADS = NCT + 32;

@@ -60,8 +60,20 @@ def test_clock_summary_parsing(tmp_path):
 
 
 def test_traffic_summary_requires_the_profiled_source(tmp_path, monkeypatch):
-    v = bench.read_traffic_summary()
-    assert v is None or v > 0
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "paper_1809_10573_gb300" / "csrc").mkdir(parents=True)
+    src = "int f(int a) {  // one\n  /* two */ return a + 1;\n}\n"
+    (tmp_path / "paper_1809_10573_gb300" / "csrc" / "apply.cu").write_text(src)
+    (tmp_path / "profiles" / "level_kernel_traffic.txt").write_text(
+        "# c\ndram_bytes_per_algorithmic_byte = 1.25\napply_cu_code_sha256 = " + bench.code_digest(src) + "\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.read_traffic_summary() == 1.25
+    # a comment edit keeps the figure, a code edit voids it
+    (tmp_path / "paper_1809_10573_gb300" / "csrc" / "apply.cu").write_text(
+        "int f(int a) {  // changed comment\n\n  /* x\n y */ return a + 1;\n}\n")
+    assert bench.read_traffic_summary() == 1.25
+    (tmp_path / "paper_1809_10573_gb300" / "csrc" / "apply.cu").write_text("int f(int a) { return a + 2; }\n")
+    assert bench.read_traffic_summary() is None
 
 
 def test_level_variants_option_parsing():
