@@ -123,3 +123,25 @@ def test_invalid_leaf_offsets():
     for bad in (np.arange(0, N + 1, 16)[:4], np.r_[0, 9, 8, np.arange(24, N + 1, 8)], np.r_[good[:-1], N - 1]):
         with pytest.raises(ValueError):
             idbf.build(K, om, xs, 1e-6, None, leaves=(bad, good))
+
+
+def test_example3_settings_of_the_paper():
+    # Fig. N: (eps, k) = (1e-6, min{m,n}) and (1e-6, 30) give O(eps); (1e-15, 30) is near machine
+    # precision. Stored entries grow like N log N (at most N log^2 N, Sec. 3).
+    K = kernels.Kernel(kernels.KIND_DFT, sign=-1)
+    per = []
+    for N in (1000, 2000, 4000):
+        om, xs = inputs.nufft_points(N, seed=N)
+        L = idbf.levels_for(N, 8)
+        lv = (idbf.dyadic_leaves(om, -N / 2, N / 2, L), idbf.dyadic_leaves(xs, 0.0, 1.0, L))
+        g = inputs.complex_gaussian(N, 1, seed=1)[:, 0]
+        ud = idbf.dense_matvec(K, om, xs, g)
+        F = idbf.build(K, om, xs, 1e-6, None, leaves=lv)
+        assert idbf.relative_error(idbf.apply(F, g), ud) < 1e-5
+        per.append(sum(s["nnz"] for s in idbf.stats(F)) / (N * np.log2(N)))
+        if N == 1000:
+            F = idbf.build(K, om, xs, 1e-15, None, rank_cap=30, leaves=lv)
+            assert idbf.relative_error(idbf.apply(F, g), ud) < 1e-13
+            F = idbf.build(K, om, xs, 1e-6, None, rank_cap=30, leaves=lv)
+            assert idbf.relative_error(idbf.apply(F, g), ud) < 1e-5
+    assert max(per) / min(per) < 1.5
