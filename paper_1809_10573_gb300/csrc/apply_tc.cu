@@ -4,7 +4,7 @@
 // cols x R) becomes a dense GEMM (Eq. 1 applied to a block of vectors). The complex product is
 // embedded in real arithmetic with interleaved real / imaginary parts and computed transposed,
 // D^T = G^T M_c^T, so that the tensor core's M dimension is 128 right-hand sides and its N
-// dimension the 2 rows real output rows of the block (accumulators in TMEM, up to 384 columns):
+// dimension 128 of the block's 2 x rows real output rows per pass (accumulators in TMEM):
 //   A (M = 128 rhs x K = 2 cols):  A(n, 2k) = Re G(k, n),  A(n, 2k+1) = Im G(k, n)
 //   B (N = 2 rows x K = 2 cols):   B(2r, 2k) = Re M(r,k), B(2r, 2k+1) = -Im M(r,k),
 //                                  B(2r+1, 2k) = Im M(r,k), B(2r+1, 2k+1) = Re M(r,k)

@@ -11,7 +11,9 @@
 // (its results are invalid), bit 0 of the status word is set, and idbf_batch_sync_status reports
 // IDBF_ETIMEOUT.
 //
-// Each node is computed by fwd_node (level_kernels.cuh), the same body as the per-level kernel.
+// Each node is computed by fwd_node (right-hand sides per thread) or fwd_node_tiled (register
+// tiles), the bodies of the per-level kernels (level_kernels.cuh); the tile, or a per-level mix
+// of the two by block height, is autotuned.
 #include <cuda_runtime.h>
 #include <string.h>
 
