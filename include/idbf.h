@@ -142,7 +142,10 @@ typedef struct {
 } idbf_host_factors;
 
 /* idbf_import_factors - copy factors given in host memory into a new plan stored in format
- * `storage`. Every size and index is validated (EFORMAT on any inconsistency). Synchronous. */
+ * `storage`. Every size and index is validated before any device work (EFORMAT on any
+ * inconsistency). Leaves must hold n0 >= 1 points each with N = n0 2^L, and every segment
+ * must be non-empty: factors on coordinate-based trees with leaves of uneven size (Example 3
+ * with random points) are refused with EINVAL. Synchronous. */
 idbf_status idbf_import_factors(const idbf_host_factors* f, int32_t storage, void* stream,
                                 idbf_plan* out);
 
