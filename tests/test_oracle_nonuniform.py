@@ -145,3 +145,13 @@ def test_example3_settings_of_the_paper():
             F = idbf.build(K, om, xs, 1e-6, None, rank_cap=30, leaves=lv)
             assert idbf.relative_error(idbf.apply(F, g), ud) < 1e-5
     assert max(per) / min(per) < 1.5
+
+
+def test_nufft_points_generator():
+    om, xs = inputs.nufft_points(1000, seed=3)
+    assert om.size == xs.size == 1000
+    assert om.min() >= -500 and om.max() < 500 and xs.min() >= 0 and xs.max() < 1
+    assert np.all(np.diff(om) >= 0) and np.all(np.diff(xs) >= 0)
+    om2, xs2 = inputs.nufft_points(1000, seed=3)
+    assert np.array_equal(om, om2) and np.array_equal(xs, xs2)
+    assert not np.array_equal(om, inputs.nufft_points(1000, seed=4)[0])
