@@ -116,6 +116,28 @@ void idbf_default_params(idbf_params* p);
 idbf_status idbf_build(const idbf_kernel* kernel, const double* x_host, const double* xi_host,
                        int64_t N, const idbf_params* params, void* stream, idbf_plan* out);
 
+/* idbf_build_leaves - idbf_build on trees whose 2^L leaves are given by offsets: the dyadic
+ * trees of Sec. 1 built by partitioning the domains of X and Omega (coordinate-based trees; see
+ * idbf_dyadic_leaves), as Example 3 needs for randomly placed points. Row leaf j holds the points
+ * x_host[row_leaf_off[j] .. row_leaf_off[j+1]) and column leaf j the points
+ * xi_host[col_leaf_off[j] .. col_leaf_off[j+1]); offsets rise from 0 to N (2^L + 1 each, host
+ * memory), leaves may be empty, N is any size >= 1, L >= 2, params->leaf is ignored. An ID of a
+ * block with no rows or no sampled columns has rank 0 (no skeleton, every index redundant). The
+ * plan runs the per-node level kernels only (see idbf_import_factors). Otherwise as idbf_build.
+ * Errors: EINVAL (offsets, L, unsorted points, params), ENOMEM, ECUDA. */
+idbf_status idbf_build_leaves(const idbf_kernel* kernel, const double* x_host, const double* xi_host,
+                              int64_t N, int32_t L, const int64_t* row_leaf_off,
+                              const int64_t* col_leaf_off, const idbf_params* params, void* stream,
+                              idbf_plan* out);
+
+/* idbf_dyadic_leaves - the leaves of the dyadic tree of depth L over the domain [lo, hi) (Sec. 1):
+ * leaf j is [lo + (hi - lo) (j / 2^L), lo + (hi - lo) ((j + 1) / 2^L)), so that a point on an
+ * interior edge belongs to the leaf on its right; off[j] (2^L + 1 entries, host memory) is the
+ * number of points below the left edge of leaf j and off[2^L] = n. points: n ascending host
+ * doubles inside [lo, hi). Host computation, no GPU work. Errors: EINVAL. */
+idbf_status idbf_dyadic_leaves(const double* points, int64_t n, double lo, double hi, int32_t L,
+                               int64_t* off);
+
 /* idbf_kernel_matvec_rows - ground truth of Sec. 3 (the direct matvec u^d) on selected rows:
  *   y[r] = sum_{j < N} K(x[rows[r]], xi[j]) v[j],  r < nrows,
  * O(nrows N) FP64 work on the current device. x, xi: N doubles; rows: nrows int64 row indices
@@ -139,13 +161,24 @@ typedef struct {
   int64_t mat_len;
   const int32_t* idx;      /* idx_len int32 indices */
   int64_t idx_len;
+  /* Leaves of uneven size (coordinate-based dyadic trees of Sec. 1, Example 3): m + 1 offsets
+   * each, rising from 0 to N; leaf j of x (columns, read by level 0) is x[col_leaf_off[j] ..
+   * col_leaf_off[j+1]) and leaf j of y (rows, written by level L) is y[row_leaf_off[j] ..
+   * row_leaf_off[j+1]). Leaves and segments may be empty. NULL (both) = leaves of n0 points. */
+  const int64_t* row_leaf_off;
+  const int64_t* col_leaf_off;
 } idbf_host_factors;
 
 /* idbf_import_factors - copy factors given in host memory into a new plan stored in format
  * `storage`. Every size and index is validated before any device work (EFORMAT on any
- * inconsistency). Leaves must hold n0 >= 1 points each with N = n0 2^L, and every segment
- * must be non-empty: factors on coordinate-based trees with leaves of uneven size (Example 3
- * with random points) are refused with EINVAL. Synchronous. */
+ * inconsistency). Without leaf offsets, leaves hold n0 >= 1 points each with N = n0 2^L and
+ * every segment is non-empty. With leaf offsets (Example 3: random points, coordinate-based
+ * trees), N is any size >= 1, n0 is ignored (0), leaves and segments may be empty, and blocks
+ * with no columns contribute zeros. Plans with leaves of uneven size run the per-node level
+ * kernels only (FP64, double-float and FP32, any number of right-hand sides, forward and
+ * adjoint, idbf_apply_noalloc): the streaming, warp, register-tiled and tensor-core kernels,
+ * batches and checkpoints refuse them with EUNSUPPORTED. Offsets that are all equal are the
+ * uniform case. Synchronous. */
 idbf_status idbf_import_factors(const idbf_host_factors* f, int32_t storage, void* stream,
                                 idbf_plan* out);
 
@@ -155,6 +188,11 @@ idbf_status idbf_import_factors(const idbf_host_factors* f, int32_t storage, voi
 #define IDBF_MODE_FP32 2   /* C64 storage, complex64 vectors, FP32 FMA */
 #define IDBF_MODE_TF32X3 3 /* C64 storage, complex64 vectors, 3xTF32 tensor-core block products
                            * (tcgen05, FP32 accumulation; forward only; blocks of <= 256 rows) */
+#define IDBF_MODE_TF32X3_S64 4 /* as IDBF_MODE_TF32X3 on every level but the middle factor S^h
+                               * (Eq. finishIDBF), whose products and sums run on the CUDA cores
+                               * in double-float (DF64 storage of that level, preferred) or FP64
+                               * (C128 storage); complex64 vectors on both of its sides. Needs C64
+                               * on the other levels (see idbf_set_level_storage); forward only */
 
 /* idbf_apply - y = K x for an N x nrhs block: x -> V levels -> S -> U levels -> y.
  *   x, y: device pointers (may not alias), ld >= N, element type set by `mode` (above).
@@ -169,25 +207,33 @@ idbf_status idbf_apply(idbf_plan plan, const void* x, void* y, int64_t nrhs, int
 idbf_status idbf_apply_adjoint(idbf_plan plan, const void* x, void* y, int64_t nrhs, int64_t ld,
                                int32_t mode, void* stream);
 
-/* idbf_apply_noalloc - y = K x exactly as idbf_apply (same arguments, modes and results), except
- * that the library allocates no device memory during the call. The paper has no counterpart of
- * this call; it exists for callers that must not allocate: a framework whose own caching
- * allocator already holds nearly all device memory (a cudaMalloc would fail or fragment it), a
- * latency-critical serving loop that cannot absorb the device-wide synchronisation that
- * cudaMalloc and cudaFree imply, or a process that has to know its full device footprint when
- * the library loads.
+/* idbf_apply_noalloc - y = K x like idbf_apply, except that the library allocates no device
+ * memory during the call. The paper has no counterpart of this call; it exists for callers that
+ * must not allocate: a framework whose own caching allocator already holds nearly all device
+ * memory (a cudaMalloc would fail or fragment it), a latency-critical serving loop that cannot
+ * absorb the device-wide synchronisation that cudaMalloc and cudaFree imply, or a process that
+ * has to know its full device footprint when the library loads.
+ *   Scope: forward apply only, modes IDBF_MODE_FP64, IDBF_MODE_DF64 and IDBF_MODE_FP32 (same
+ *   arguments as idbf_apply). Every level runs the per-node level kernel (variant 0 of
+ *   idbf_autotune), not the autotuned streaming or register-tiled kernels, so a call is slower
+ *   than idbf_apply and its double-float / FP32 results differ from idbf_apply's in the summation
+ *   order only: they agree within that mode's rounding error (FP64: to ~1e-15 relative).
  *   Workspace: a fixed array of IDBF_NOALLOC_SCRATCH_BYTES compiled into the library. Every GPU
  *   that loads the library holds one such array until the process exits. A call needs
  *   32 * nrhs * segment_entries bytes (segment_entries as reported by idbf_stats); a larger
  *   request returns IDBF_EUNSUPPORTED before any GPU work (the FIO benchmark kernel fits for
- *   N up to 2^18 with one right-hand side).
+ *   N up to 2^18 with one right-hand side), as does a level whose per-node kernel would need
+ *   more than 200 KB of shared memory (all levels are checked before the first launch).
  *   The first call on each device looks up the array's device address (cudaGetSymbolAddress,
- *   with that device current): make that first call before any stream capture.
+ *   with that device current) and caches it for the life of the process's primary context on
+ *   that device (after cudaDeviceReset no plan, and no cached address, remains valid): make that
+ *   first call before any stream capture.
  *   All calls on a device share the one array, and it keeps whatever the previous call left in
  *   it; nothing in it has to start at zero, because every level overwrites each segment before
  *   the next level reads it. Calls whose GPU work overlaps (other streams, other plans, other
  *   host threads) race on the array and produce wrong results: serialise them.
- *   Errors: EINVAL, EUNSUPPORTED (size above the limit, or storage for `mode` absent), ECUDA. */
+ *   Errors: EINVAL (also for IDBF_MODE_TF32X3), EUNSUPPORTED (size above the limit, or storage
+ *   for `mode` absent), ECUDA. */
 #define IDBF_NOALLOC_SCRATCH_BYTES (64ull << 20)
 idbf_status idbf_apply_noalloc(idbf_plan plan, const void* x, void* y, int64_t nrhs, int64_t ld,
                                int32_t mode, void* stream);
@@ -220,6 +266,12 @@ idbf_status idbf_set_tc_split(idbf_plan plan, int32_t split_mode);
 /* idbf_reserve - allocate the apply workspace for up to nrhs right-hand sides now. */
 idbf_status idbf_reserve(idbf_plan plan, int64_t nrhs);
 
+/* idbf_set_level_storage - as idbf_set_storage for level `level` (0..L, apply order) alone, e.g.
+ * to keep the middle factor (level h_V = floor(L/2)) in C128 or DF64 for IDBF_MODE_TF32X3_S64
+ * while every other level holds C64 only. Synchronous. Errors: EINVAL, EUNSUPPORTED (a wider
+ * format asked of a level that holds only C64), ENOMEM, ECUDA. */
+idbf_status idbf_set_level_storage(idbf_plan plan, int32_t level, uint32_t mask, void* stream);
+
 /* idbf_set_storage - keep exactly the formats in `mask` (bit IDBF_STORE_*). Missing formats
  * are converted from a present one (C128 preferred as the source; C128 <-> DF64 in place when
  * only one of them is kept). Stream-ordered; ENOMEM leaves the plan unchanged. */
@@ -241,7 +293,8 @@ typedef struct idbf_batch_s* idbf_batch;
 
 /* idbf_batch_create - prepare the forward apply of nops plans (any N each), plan o with nrhs[o]
  * right-hand sides, in `mode` (FP64, DF64 or FP32), as ONE persistent kernel launch captured in a
- * CUDA graph. Work items (operator, level, run of nodes, block of right-hand sides) are queued in
+ * CUDA graph (plans with leaves of n0 points; uneven leaves: EUNSUPPORTED). Work items
+ * (operator, level, run of nodes, block of right-hand sides) are queued in
  * level order and taken by persistent CTAs; an item waits (bounded) until the previous level of
  * its operator is complete. Allocates each operator's level workspace; the plans must outlive
  * the batch and must not be changed (storage) while it exists. Synchronous. */
@@ -307,6 +360,7 @@ typedef struct {
   double build_seconds;                    /* wall time of idbf_build (0 for imported plans) */
   int64_t device_bytes;                    /* device memory held by the plan */
   int32_t level_variant[3][IDBF_MAX_LEVELS]; /* forward kernel per storage format and level (-1: default) */
+  uint32_t level_storage[IDBF_MAX_LEVELS];   /* storage formats held by level l (bit IDBF_STORE_*) */
 } idbf_stats_t;
 
 /* idbf_stats - fill *s (host memory). Synchronous, no GPU work. */
@@ -318,6 +372,12 @@ idbf_status idbf_stats(idbf_plan plan, idbf_stats_t* s);
  * idbf_load - read such a file into a new plan stored as `storage`. EFORMAT on a bad file. */
 idbf_status idbf_save(idbf_plan plan, const char* path);
 idbf_status idbf_load(const char* path, int32_t storage, void* stream, idbf_plan* out);
+
+/* idbf_clone - a new plan on the same device holding a device-to-device copy of every factor,
+ * index list and storage format of `plan` (and its autotuned level variants), e.g. to give
+ * identical operators of a batch factor memory of their own without building them again.
+ * Synchronous on `stream`. Errors: EINVAL (NULL, other device current), ENOMEM, ECUDA. */
+idbf_status idbf_clone(idbf_plan plan, void* stream, idbf_plan* out);
 
 /* idbf_destroy - free the plan and all device memory it owns (NULL is a no-op). Synchronises
  * the device first so that no queued work still reads the factors. */

@@ -14,15 +14,15 @@ import torch
 
 from . import _lib
 from ._lib import (KERNEL_DFT, KERNEL_FIO1D, KERNEL_J0, MODE_DF64, MODE_FP32, MODE_FP64, MODE_TF32X3,
-                   NUM_FWD_VARIANTS, SAMPLE_ALL, SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, STORE_C64, STORE_C128,
+                   MODE_TF32X3_S64, NUM_FWD_VARIANTS, SAMPLE_ALL, SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, STORE_C64, STORE_C128,
                    STORE_DF64, IDBFError)
 
-__all__ = ["Plan", "Batch", "IDBFError", "apply", "IDBFApply", "kernel_matvec_rows", "KERNEL_FIO1D", "KERNEL_DFT", "KERNEL_J0", "MODE_FP64",
-           "MODE_DF64", "MODE_FP32", "MODE_TF32X3", "STORE_C128", "STORE_DF64", "STORE_C64",
+__all__ = ["Plan", "Batch", "IDBFError", "apply", "IDBFApply", "kernel_matvec_rows", "dyadic_leaves", "tree_depth", "KERNEL_FIO1D", "KERNEL_DFT", "KERNEL_J0", "MODE_FP64",
+           "MODE_DF64", "MODE_FP32", "MODE_TF32X3", "MODE_TF32X3_S64", "STORE_C128", "STORE_DF64", "STORE_C64",
            "SAMPLE_MOCK_CHEBYSHEV", "SAMPLE_RANDOM", "SAMPLE_ALL", "NUM_FWD_VARIANTS"]
 
 _VEC_DTYPE = {MODE_FP64: torch.complex128, MODE_DF64: torch.complex128,
-              MODE_FP32: torch.complex64, MODE_TF32X3: torch.complex64}
+              MODE_FP32: torch.complex64, MODE_TF32X3: torch.complex64, MODE_TF32X3_S64: torch.complex64}
 
 
 def _stream_ptr(stream=None):
@@ -74,6 +74,31 @@ class Plan:
         return plan
 
     @classmethod
+    def build_leaves(cls, x, xi, L, row_leaf_off, col_leaf_off, eps=1e-6, kernel="dft", c_profile=0, sign=-1,
+                     rank_cap=0, oversample=1.0, oversample_leaf=0.0, sampling=SAMPLE_MOCK_CHEBYSHEV, seed=0,
+                     storage=STORE_C128, stream=None):
+        """idbf_build_leaves: the construction on trees whose 2^L leaves are given by offsets."""
+        L_ = _lib.lib()
+        k = _lib.Kernel(_kernel_kind(kernel), sign, c_profile, 0)
+        p = _lib.Params()
+        L_.idbf_default_params(C.byref(p))
+        p.eps, p.rank_cap, p.oversample, p.oversample_leaf = eps, rank_cap, oversample, oversample_leaf
+        p.sampling, p.seed, p.storage = sampling, seed, storage
+        xa = np.ascontiguousarray(x, dtype=np.float64)
+        xia = np.ascontiguousarray(xi, dtype=np.float64)
+        ro = np.ascontiguousarray(row_leaf_off, dtype=np.int64)
+        co = np.ascontiguousarray(col_leaf_off, dtype=np.int64)
+        if ro.size != (1 << L) + 1 or co.size != (1 << L) + 1:
+            raise ValueError("2^L + 1 offsets per tree expected")
+        out = C.c_void_p()
+        st = L_.idbf_build_leaves(C.byref(k), xa.ctypes.data, xia.ctypes.data, xa.size, int(L), ro.ctypes.data,
+                                  co.ctypes.data, C.byref(p), _stream_ptr(stream), C.byref(out))
+        _lib.check(st, "idbf_build_leaves")
+        plan = cls(out.value, torch.cuda.current_device())
+        plan.rank_capped = st == _lib.ERANKCAP
+        return plan
+
+    @classmethod
     def import_factors(cls, ex: dict, storage=STORE_C128, stream=None):
         """Import factors given in the butterfly layout (a dict of numpy arrays)."""
         L = _lib.lib()
@@ -88,6 +113,10 @@ class Plan:
                              keep["rows"].ctypes.data, keep["cols"].ctypes.data, keep["moff"].ctypes.data,
                              keep["ioff"].ctypes.data, keep["mat"].ctypes.data, keep["mat"].size,
                              keep["idx"].ctypes.data, keep["idx"].size)
+        if int(ex["n0"]) == 0:  # leaves of uneven size (coordinate-based trees): pass their offsets
+            keep["ro"] = np.ascontiguousarray(ex["row_leaf_off"], dtype=np.int64)
+            keep["co"] = np.ascontiguousarray(ex["col_leaf_off"], dtype=np.int64)
+            f.row_leaf_off, f.col_leaf_off = keep["ro"].ctypes.data, keep["co"].ctypes.data
         out = C.c_void_p()
         _lib.check(L.idbf_import_factors(C.byref(f), storage, _stream_ptr(stream), C.byref(out)),
                    "idbf_import_factors")
@@ -98,6 +127,12 @@ class Plan:
         out = C.c_void_p()
         _lib.check(_lib.lib().idbf_load(path.encode(), storage, _stream_ptr(stream), C.byref(out)), "idbf_load")
         return cls(out.value, torch.cuda.current_device())
+
+    def clone(self, stream=None) -> "Plan":
+        """A copy of this plan with factor memory of its own (idbf_clone)."""
+        out = C.c_void_p()
+        _lib.check(_lib.lib().idbf_clone(self._h, _stream_ptr(stream), C.byref(out)), "idbf_clone")
+        return Plan(out.value, self.device)
 
     def save(self, path: str):
         _lib.check(_lib.lib().idbf_save(self._h, path.encode()), "idbf_save")
@@ -157,6 +192,14 @@ class Plan:
             mask |= 1 << f
         _lib.check(_lib.lib().idbf_set_storage(self._h, mask, _stream_ptr(stream)), "idbf_set_storage")
 
+    def set_level_storage(self, level: int, *formats, stream=None):
+        """Keep exactly `formats` on one level (apply order 0..L)."""
+        mask = 0
+        for f in formats:
+            mask |= 1 << f
+        _lib.check(_lib.lib().idbf_set_level_storage(self._h, int(level), mask, _stream_ptr(stream)),
+                   "idbf_set_level_storage")
+
     def stats(self) -> dict:
         s = _lib.Stats()
         _lib.check(_lib.lib().idbf_stats(self._h, C.byref(s)), "idbf_stats")
@@ -166,7 +209,8 @@ class Plan:
                     level_entries=list(s.level_entries[:nl]), level_kmin=list(s.level_kmin[:nl]),
                     level_kmax=list(s.level_kmax[:nl]), segment_entries=s.segment_entries,
                     build_seconds=s.build_seconds, device_bytes=s.device_bytes,
-                    level_variant={f: list(s.level_variant[f][:nl]) for f in range(3)})
+                    level_variant={f: list(s.level_variant[f][:nl]) for f in range(3)},
+                    level_storage=list(s.level_storage[:nl]))
 
     def algorithmic_bytes(self, nrhs: int = 1, entry_bytes: int = 16, vec_bytes: int = 16) -> int:
         """Bytes one apply must move at least: every stored factor entry once, the int32
@@ -262,6 +306,25 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def dyadic_leaves(points, lo: float, hi: float, L: int):
+    """Offsets (2^L + 1) of the leaves of the dyadic tree of depth L over [lo, hi) (Sec. 1), computed
+    by the library (idbf_dyadic_leaves)."""
+    p = np.ascontiguousarray(points, dtype=np.float64)
+    off = np.zeros((1 << L) + 1, dtype=np.int64)
+    _lib.check(_lib.lib().idbf_dyadic_leaves(p.ctypes.data, p.size, float(lo), float(hi), int(L), off.ctypes.data),
+               "idbf_dyadic_leaves")
+    return off
+
+
+def tree_depth(N: int, n0: int) -> int:
+    """Depth of a coordinate-based tree for N points with about n0 per leaf: the L whose mean leaf
+    size N / 2^L is nearest to n0 on a log scale, at least 2."""
+    import math
+    if N < 1 or n0 < 1:
+        raise ValueError("N and n0 must be positive")
+    return max(2, int(round(math.log2(N / n0))))
 
 
 def _kernel_kind(name: str) -> int:

@@ -15,7 +15,7 @@ OK, EINVAL, ENOMEM, ECUDA, ERANKCAP, ETIMEOUT, EFORMAT, EUNSUPPORTED = range(8)
 KERNEL_FIO1D, KERNEL_DFT, KERNEL_J0 = 0, 1, 2
 SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, SAMPLE_ALL = 0, 1, 2
 STORE_C128, STORE_DF64, STORE_C64 = 0, 1, 2
-MODE_FP64, MODE_DF64, MODE_FP32, MODE_TF32X3 = 0, 1, 2, 3
+MODE_FP64, MODE_DF64, MODE_FP32, MODE_TF32X3, MODE_TF32X3_S64 = 0, 1, 2, 3, 4
 NUM_FWD_VARIANTS = 16  # IDBF_NUM_FWD_VARIANTS
 MAX_LEVELS = 48
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -35,7 +35,8 @@ class HostFactors(C.Structure):
     _fields_ = [("N", C.c_int64), ("n0", C.c_int32), ("L", C.c_int32),
                 ("seg_len", C.c_void_p), ("blk_rows", C.c_void_p), ("blk_cols", C.c_void_p),
                 ("blk_moff", C.c_void_p), ("blk_ioff", C.c_void_p),
-                ("mat", C.c_void_p), ("mat_len", C.c_int64), ("idx", C.c_void_p), ("idx_len", C.c_int64)]
+                ("mat", C.c_void_p), ("mat_len", C.c_int64), ("idx", C.c_void_p), ("idx_len", C.c_int64),
+                ("row_leaf_off", C.c_void_p), ("col_leaf_off", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -45,7 +46,7 @@ class Stats(C.Structure):
                 ("level_entries", C.c_int64 * MAX_LEVELS), ("level_kmin", C.c_int32 * MAX_LEVELS),
                 ("level_kmax", C.c_int32 * MAX_LEVELS), ("segment_entries", C.c_int64),
                 ("build_seconds", C.c_double), ("device_bytes", C.c_int64),
-                ("level_variant", (C.c_int32 * MAX_LEVELS) * 3)]
+                ("level_variant", (C.c_int32 * MAX_LEVELS) * 3), ("level_storage", C.c_uint32 * MAX_LEVELS)]
 
 
 _lib = None
@@ -55,6 +56,9 @@ SIGNATURES = {
     "idbf_default_params": (None, [C.POINTER(Params)]),
     "idbf_build": (C.c_int, [C.POINTER(Kernel), C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(Params),
                              C.c_void_p, C.POINTER(C.c_void_p)]),
+    "idbf_build_leaves": (C.c_int, [C.POINTER(Kernel), C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                                    C.c_void_p, C.POINTER(Params), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "idbf_dyadic_leaves": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_int32, C.c_void_p]),
     "idbf_kernel_matvec_rows": (C.c_int, [C.POINTER(Kernel), C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                           C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "idbf_import_factors": (C.c_int, [C.POINTER(HostFactors), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -70,6 +74,7 @@ SIGNATURES = {
     "idbf_sync_status": (C.c_int, [C.c_void_p, C.c_void_p]),
     "idbf_debug_set_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32]),
     "idbf_set_storage": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p]),
+    "idbf_set_level_storage": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint32, C.c_void_p]),
     "idbf_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "idbf_batch_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     "idbf_batch_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -83,6 +88,7 @@ SIGNATURES = {
     "idbf_batch_destroy": (None, [C.c_void_p]),
     "idbf_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "idbf_load": (C.c_int, [C.c_char_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "idbf_clone": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     "idbf_destroy": (None, [C.c_void_p]),
     "idbf_strerror": (C.c_char_p, [C.c_int]),
     "idbf_last_cuda_error": (C.c_char_p, []),

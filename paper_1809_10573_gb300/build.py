@@ -20,7 +20,9 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libidbf.so")
 SOURCES = ["plan.cu", "apply.cu", "apply_tc.cu", "batch.cu", "build_gpu.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+# host code: no contraction of a * b + c into an FMA, so that host arithmetic (e.g. the dyadic leaf
+# edges) rounds the same on x86-64 and aarch64
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
 

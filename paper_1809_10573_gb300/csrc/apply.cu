@@ -77,11 +77,12 @@ __global__ void __launch_bounds__(256) k_level_adj(DevLevel d, const typename P:
   // phase 1: adjoint inputs (forward outputs) -> v
   int o0len, o1len;
   if (d.lev == d.L) {
-    o0len = d.n0;
+    o0len = leaf_len(d, j);
     o1len = 0;
+    const int64_t x0 = leaf_start(d, j);
     for (int i = tid; i < o0len * RB; i += nt) {
       const int e = i / RB, rb = i % RB;
-      v[i] = rb < nrb ? io.x[j * d.n0 + e + (int64_t)(r0 + rb) * io.ldx] : P::zero();
+      v[i] = rb < nrb ? io.x[x0 + e + (int64_t)(r0 + rb) * io.ldx] : P::zero();
     }
   } else {
     const int64_t s0 = out_seg_id(d, j, 0), s1 = out_seg_id(d, j, 1);
@@ -176,9 +177,10 @@ __global__ void __launch_bounds__(256) k_level_adj(DevLevel d, const typename P:
   }
   __syncthreads();
   if (d.lev == 0) {
+    const int64_t y0 = leaf_start(d, j);
     for (int k = tid; k < nin * nrb; k += nt) {
       const int e = k / nrb, rb = k % nrb;
-      io.y[j * d.n0 + e + (int64_t)(r0 + rb) * io.ldy] = ub[e * RB + rb];
+      io.y[y0 + e + (int64_t)(r0 + rb) * io.ldy] = ub[e * RB + rb];
     }
   } else {
     const int len0 = d.in_len[2 * j];
@@ -766,6 +768,7 @@ static idbf_status launch_fwd_variant(Plan* p, int l, int v, const void* x, void
   IO<V> io;
   io.x = (const V*)x; io.ldx = p->N; io.y = (V*)y; io.ldy = p->N; io.R = 1;
   io.win = win; io.wout = wout;
+  if (v != 0 && p->uneven) return IDBF_EUNSUPPORTED;  // uneven leaves: the per-node kernel only
   if (v == 7) return launch_warp_node<P>(p, l, io, st, fmt);
   if (v != 0 && fmt == IDBF_STORE_C128) return IDBF_EUNSUPPORTED;  // FP64: per-node or warp-per-node kernel
   if (v == 14 || v == 15) return launch_stream<P, strm::RingD>(p, l, v == 14, true, x, io, st);
@@ -838,14 +841,15 @@ static idbf_status run_levels(Plan* p, const void* x, void* y, int64_t R, int64_
     dim3 grid((unsigned)p->m, (unsigned)((R + RB - 1) / RB));
     if (!adjoint && RB == 1) {
       // one right-hand side, forward: the per-level variant (autotuned, else the default)
-      const int v = p->tuned[fmt].size() > (size_t)l && p->tuned[fmt][l] >= 0 ? p->tuned[fmt][l] : default_variant(fmt);
+      const int v = p->uneven ? 0
+                    : p->tuned[fmt].size() > (size_t)l && p->tuned[fmt][l] >= 0 ? p->tuned[fmt][l] : default_variant(fmt);
       idbf_status s = launch_fwd_variant<P>(p, l, v, x, y, io.win, io.wout, st, fmt);
       if (s == IDBF_EUNSUPPORTED && v != 0) s = launch_fwd_variant<P>(p, l, 0, x, y, io.win, io.wout, st, fmt);
       if (s != IDBF_OK) return s;
       continue;
     }
     if constexpr (RB >= 8 && tiled_ok<P>()) {
-      if (!adjoint) {
+      if (!adjoint && !p->uneven) {
       // several right-hand sides, FP32 / FP64: register tiles over streamed factor columns
       // short blocks: 128 threads per CTA, so that more nodes (each a chain of dependent memory
       // accesses) are in flight per SM
@@ -880,7 +884,7 @@ static idbf_status run_levels(Plan* p, const void* x, void* y, int64_t R, int64_
       if constexpr (RB >= 8 && tiled_ok<P>()) {
         // several right-hand sides, FP32 / FP64: register tiles over streamed row chunks
         const size_t sm = tadj::smem_bytes<P, RB>(li.max_in, li.max_out, li.max_rows, li.max_cols);
-        if (sm <= 200 * 1024) {
+        if (sm <= 200 * 1024 && !p->uneven) {
           constexpr bool f32 = sizeof(V) == 8;
           auto kern = k_level_adj_tiled<P, RB, f32 ? 2 : 1>;
           if (sm > 48 * 1024) IDBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -916,14 +920,24 @@ static idbf_status apply_common(idbf_plan h, const void* x, void* y, int64_t nrh
     case IDBF_MODE_DF64: fmt = IDBF_STORE_DF64; break;
     case IDBF_MODE_FP32: fmt = IDBF_STORE_C64; break;
     case IDBF_MODE_TF32X3: fmt = IDBF_STORE_C64; break;
+    case IDBF_MODE_TF32X3_S64: fmt = IDBF_STORE_C64; break;
     default: return IDBF_EINVAL;
   }
-  if (!p->has_format(fmt)) return IDBF_EUNSUPPORTED;
-  if (mode == IDBF_MODE_TF32X3 && adjoint) return IDBF_EUNSUPPORTED;
+  const bool tensor = mode == IDBF_MODE_TF32X3 || mode == IDBF_MODE_TF32X3_S64;
+  if (mode == IDBF_MODE_TF32X3_S64) {
+    // complex64 on every level but the middle one, which needs C128 or DF64
+    for (int l = 0; l <= p->L; ++l)
+      if (l != p->hV && p->lmat_len[l] > 0 && !p->lmat[IDBF_STORE_C64][l]) return IDBF_EUNSUPPORTED;
+    if (p->lmat_len[p->hV] > 0 && !p->lmat[IDBF_STORE_C128][p->hV] && !p->lmat[IDBF_STORE_DF64][p->hV])
+      return IDBF_EUNSUPPORTED;
+  } else if (!p->has_format(fmt)) {
+    return IDBF_EUNSUPPORTED;
+  }
+  if (tensor && adjoint) return IDBF_EUNSUPPORTED;
   idbf_status s = ensure_workspace(p, nrhs);
   if (s != IDBF_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  if (mode == IDBF_MODE_TF32X3) return apply_tf32x3(p, x, y, nrhs, ld, st);
+  if (tensor) return apply_tf32x3(p, x, y, nrhs, ld, st, mode == IDBF_MODE_TF32X3_S64);
   const bool one = nrhs == 1;
   // several right-hand sides in FP32 / FP64 (forward and adjoint): 16 per tile from 16 on, else 8
   const bool wide = nrhs >= 16, mid = nrhs > 1;
@@ -943,6 +957,43 @@ static idbf_status apply_common(idbf_plan h, const void* x, void* y, int64_t nrh
       else if (mid) s2 = run_levels<FP32P, 8>(p, x, y, nrhs, ld, adjoint, st, fmt);
       return s2 != IDBF_EUNSUPPORTED ? s2 : run_levels<FP32P, 4>(p, x, y, nrhs, ld, adjoint, st, fmt);
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// The middle factor S^h of IDBF_MODE_TF32X3_S64 (the other levels run on the tensor cores): the
+// complex64 boundaries h_V - 1 and h_V of the workspace, the products and sums in double-float
+// (DF64 storage of the level, preferred: FP32 issue) or FP64 (C128 storage: the FP64 pipes), four
+// right-hand sides per CTA, two per thread.
+idbf_status apply_middle_wide(Plan* p, const void* win, void* wout, int64_t R, cudaStream_t st) {
+  const int l = p->hV;
+  const LevelInfo& li = p->lv[l];
+  const bool df = p->lmat[IDBF_STORE_DF64][l] != nullptr;
+  if (!df && !p->lmat[IDBF_STORE_C128][l]) return IDBF_EUNSUPPORTED;
+  constexpr int RB = 4, RPT = 2, NT = 256;
+  const int gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
+  const int rcap = std::max(li.max_rows, li.max_cols);
+  const DevLevel d = p->level(l);
+  IO<float2> io;
+  io.x = nullptr; io.ldx = p->N; io.y = nullptr; io.ldy = p->N; io.R = (int)R;
+  io.win = (const float2*)win; io.wout = (float2*)wout;
+  const dim3 grid((unsigned)p->m, (unsigned)((R + RB - 1) / RB));
+  if (df) {
+    const size_t sm = fwd_node_smem<DF64S32P, RB, RPT>(li.max_in, gcap, rcap, NT);
+    if (sm > 200 * 1024) return IDBF_EUNSUPPORTED;
+    if (sm > 48 * 1024)
+      IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_fwd<DF64S32P, RB, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_level_fwd<DF64S32P, RB, RPT><<<grid, NT, sm, st>>>(d, (const float4*)p->lmat[IDBF_STORE_DF64][l], io, gcap, rcap,
+                                                         li.max_in);
+  } else {
+    const size_t sm = fwd_node_smem<FP64S32P, RB, RPT>(li.max_in, gcap, rcap, NT);
+    if (sm > 200 * 1024) return IDBF_EUNSUPPORTED;
+    if (sm > 48 * 1024)
+      IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_fwd<FP64S32P, RB, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_level_fwd<FP64S32P, RB, RPT><<<grid, NT, sm, st>>>(d, (const double2*)p->lmat[IDBF_STORE_C128][l], io, gcap, rcap,
+                                                         li.max_in);
+  }
+  IDBF_CUDA_TRY(cudaGetLastError());
+  return IDBF_OK;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -973,11 +1024,26 @@ static idbf_status noalloc_scratch(int dev, void** out) {
   return IDBF_OK;
 }
 
-// The forward level loop of run_levels with the two ping-pong buffers placed in `ws`.
+// Shared memory of the per-node forward kernel k_level_fwd<P, RB> on level l.
+template <class P, int RB>
+static size_t scratch_level_smem(const Plan* p, int l) {
+  using V = typename P::vec_t;
+  const LevelInfo& li = p->lv[l];
+  const int gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
+  const int rcap = std::max(li.max_rows, li.max_cols);
+  return (size_t)RB * (li.max_in * sizeof(V) + 2 * gcap * sizeof(typename P::gv_t) + 2 * rcap * sizeof(V) +
+                       li.max_out * sizeof(V));
+}
+
+// The forward level loop of run_levels with the two ping-pong buffers placed in `ws`. Every
+// level's shared memory is checked before the first launch, so that a refused request leaves
+// y untouched.
 template <class P, int RB>
 static idbf_status run_levels_scratch(Plan* p, const void* x, void* y, int64_t R, int64_t ld, cudaStream_t st,
                                       int fmt, void* ws) {
   using V = typename P::vec_t;
+  for (int l = 0; l <= p->L; ++l)
+    if (scratch_level_smem<P, RB>(p, l) > 200 * 1024) return IDBF_EUNSUPPORTED;
   V* wb[2] = {(V*)ws, (V*)((char*)ws + (size_t)p->max_seg_total * R * 16)};
   for (int l = 0; l <= p->L; ++l) {
     const LevelInfo& li = p->lv[l];
@@ -990,9 +1056,7 @@ static idbf_status run_levels_scratch(Plan* p, const void* x, void* y, int64_t R
     const int gcap = std::max(std::max(li.max_cols, li.max_rows), li.max_in);
     const int rcap = std::max(li.max_rows, li.max_cols);
     dim3 grid((unsigned)p->m, (unsigned)((R + RB - 1) / RB));
-    const size_t sm = (size_t)RB * (li.max_in * sizeof(V) + 2 * gcap * sizeof(typename P::gv_t) +
-                                    2 * rcap * sizeof(V) + li.max_out * sizeof(V));
-    if (sm > 200 * 1024) return IDBF_EUNSUPPORTED;
+    const size_t sm = scratch_level_smem<P, RB>(p, l);
     if (sm > 48 * 1024) IDBF_CUDA_TRY(cudaFuncSetAttribute(k_level_fwd<P, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int threads = ((li.max_rows_pair + 31) / 32) * 32;
     threads = std::max(64, std::min(512, threads));

@@ -453,10 +453,14 @@ __global__ void __launch_bounds__(NT + 32, 1)
 
 }  // namespace tc
 
-// the 3xTF32 apply of all levels (forward); returns EUNSUPPORTED if a block is too large
-idbf_status apply_tf32x3(Plan* p, const void* x, void* y, int64_t R, int64_t ld, cudaStream_t st) {
-  for (int l = 0; l <= p->L; ++l)
+// the 3xTF32 apply of all levels (forward); returns EUNSUPPORTED if a block is too large. With
+// wide_middle the middle factor S^h runs on the CUDA cores in FP64 or double-float instead.
+idbf_status apply_tf32x3(Plan* p, const void* x, void* y, int64_t R, int64_t ld, cudaStream_t st, bool wide_middle) {
+  if (p->uneven) return IDBF_EUNSUPPORTED;  // leaves of n0 points only
+  for (int l = 0; l <= p->L; ++l) {
+    if (wide_middle && l == p->hV) continue;
     if (p->lv[l].max_rows > tc::MAXROWS || p->lv[l].max_cols > tc::GIXCAP) return IDBF_EUNSUPPORTED;
+  }
   IDBF_CUDA_TRY(cudaFuncSetAttribute(tc::k_level_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM));
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -468,6 +472,11 @@ idbf_status apply_tf32x3(Plan* p, const void* x, void* y, int64_t R, int64_t ld,
     const DevLevel d = p->level(l);
     const float2* win = l > 0 ? wb[(l - 1) & 1] : nullptr;
     float2* wout = l < p->L ? wb[l & 1] : nullptr;
+    if (wide_middle && l == p->hV) {  // h_V >= 1: both sides are workspace boundaries
+      const idbf_status s = apply_middle_wide(p, win, wout, R, st);
+      if (s != IDBF_OK) return s;
+      continue;
+    }
     const unsigned ctas = (unsigned)std::min<int64_t>(p->m, sms);
     tc::k_level_tc<<<ctas, tc::NT + 32, tc::SMEM, st>>>(d, (const float2*)p->lmat[IDBF_STORE_C64][l], (const float2*)x, ld,
                                                   (float2*)y, ld, win, wout, (int)R, p->d_status, p->wait_limit_ns,

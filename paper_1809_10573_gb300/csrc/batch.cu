@@ -374,7 +374,7 @@ idbf_status idbf_batch_create(const idbf_plan* plans, int32_t nops, const int64_
   cudaGetDevice(&dev);
   for (int o = 0; o < nops; ++o) {
     if (!plans[o] || nrhs[o] < 1 || nrhs[o] > (1 << 16) || plans[o]->p.device != dev) return IDBF_EINVAL;
-    if (!plans[o]->p.has_format(fmt)) return IDBF_EUNSUPPORTED;
+    if (!plans[o]->p.has_format(fmt) || plans[o]->p.uneven) return IDBF_EUNSUPPORTED;
   }
   idbf_batch_s* b = new (std::nothrow) idbf_batch_s();
   if (!b) return IDBF_ENOMEM;

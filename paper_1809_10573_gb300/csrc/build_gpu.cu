@@ -379,7 +379,8 @@ __global__ void __launch_bounds__(NT) k_qr(const IDDesc* __restrict__ D, double2
   }
   if (tid == 0) {
     kout[blockIdx.x] = k;
-    satur[blockIdx.x] = (!zero_block && k == kmax && kmax < b) ? 1 : 0;  // stopped at the cap, not by eps
+    // stopped at the cap, not by eps (an empty block, kmax = 0, has rank 0 by definition)
+    satur[blockIdx.x] = (!zero_block && kmax > 0 && k == kmax && kmax < b) ? 1 : 0;
   }
   __syncthreads();
   if (zero_block) return;
@@ -568,6 +569,17 @@ static uint64_t stream_key(uint64_t seed, int side, int step, int64_t node) {
 idbf_status Builder::run_step(int side, int s) {
   const int L = p->L, n0 = p->n0;
   const int64_t N = p->N;
+  // leaf j of the rows (x points) and of the columns (xi points): offsets when uneven
+  auto row_leaf = [&](int64_t j, int64_t* first) -> int32_t {
+    if (!p->uneven) { *first = j * n0; return n0; }
+    *first = p->h_leaf_y[j];
+    return (int32_t)(p->h_leaf_y[j + 1] - p->h_leaf_y[j]);
+  };
+  auto col_leaves = [&](int64_t j0, int64_t j1, int64_t* first) -> int64_t {  // leaves j0 .. j1-1
+    if (!p->uneven) { *first = j0 * n0; return (j1 - j0) * n0; }
+    *first = p->h_leaf_x[j0];
+    return p->h_leaf_x[j1] - p->h_leaf_x[j0];
+  };
   const int64_t nid = 2LL * p->m;
   StepOut out;
   out.side = side;
@@ -587,10 +599,9 @@ idbf_status Builder::run_step(int side, int s) {
     if (side == 0) {
       const int64_t rho = id >> s, kappa = id & ((1LL << s) - 1);
       if (s == 1) {
-        d.b_range = rho * n0;
-        d.b = n0;
-        d.c_range = kappa * (N / 2);
-        d.n_c = N / 2;
+        d.b = row_leaf(rho, &d.b_range);
+        const int64_t half = p->m / 2;
+        d.n_c = col_leaves(kappa * half, (kappa + 1) * half, &d.c_range);
       } else {
         const int64_t kp = kappa >> 1;
         const int64_t ia = list_pos(0, s - 1, (2 * rho) * (1LL << (s - 1)) + kp);
@@ -612,8 +623,7 @@ idbf_status Builder::run_step(int side, int s) {
     } else {
       const int64_t tau = id >> (L - s + 1), sigma = id & ((1LL << (L - s + 1)) - 1);
       if (s == 1) {
-        d.b_range = sigma * n0;
-        d.b = n0;
+        d.b = (int32_t)col_leaves(sigma, sigma + 1, &d.b_range);
       } else {
         const int64_t ia = (tau >> 1) * (1LL << (L - s + 2)) + 2 * sigma;
         d.b_range = -1;
@@ -633,6 +643,7 @@ idbf_status Builder::run_step(int side, int s) {
     }
     const int64_t kp = prm.rank_cap > 0 ? prm.rank_cap : std::min<int64_t>(d.b, d.n_c);
     const int64_t want = (int64_t)ceil(t * (double)kp);
+    (void)N;
     d.ns = (int32_t)std::min<int64_t>(d.n_c, std::max<int64_t>(1, want));
     if (prm.sampling == IDBF_SAMPLE_ALL) d.ns = (int32_t)d.n_c;
     d.kmax = (int32_t)std::min<int64_t>(std::min<int64_t>(d.ns, d.b), kp);
@@ -944,15 +955,26 @@ extern "C" idbf_status idbf_kernel_matvec_rows(const idbf_kernel* kernel, const 
   return IDBF_OK;
 }
 
-extern "C" idbf_status idbf_build(const idbf_kernel* kernel, const double* x_host, const double* xi_host, int64_t N,
-                                  const idbf_params* params, void* stream, idbf_plan* out) {
+// The construction for uniform leaves (ro = co = nullptr, leaf size params->leaf) or for leaves
+// given by offsets (2^L + 1 each; params->leaf unused).
+static idbf_status build_plan(const idbf_kernel* kernel, const double* x_host, const double* xi_host, int64_t N,
+                              int L, const int64_t* ro, const int64_t* co, const idbf_params* params, void* stream,
+                              idbf_plan* out) {
   if (!out) return IDBF_EINVAL;
   *out = nullptr;
   if (!kernel || !x_host || !xi_host || !params) return IDBF_EINVAL;
   const idbf_params& pr = *params;
-  if (pr.leaf < 1 || N < 4 * (int64_t)pr.leaf || N % pr.leaf || N > (1LL << 31) - 1) return IDBF_EINVAL;
-  const int64_t m = N / pr.leaf;
-  if (m & (m - 1)) return IDBF_EINVAL;
+  const bool uneven = ro != nullptr;
+  if (N < 1 || N > (1LL << 31) - 1 || L < 2 || L > 30) return IDBF_EINVAL;
+  const int64_t m = 1LL << L;
+  if (!uneven && (pr.leaf < 1 || N != (int64_t)pr.leaf * m)) return IDBF_EINVAL;
+  if (uneven) {
+    for (const int64_t* o : {ro, co}) {
+      if (o[0] != 0 || o[m] != N) return IDBF_EINVAL;
+      for (int64_t j = 0; j < m; ++j)
+        if (o[j + 1] < o[j]) return IDBF_EINVAL;
+    }
+  }
   if (!(pr.eps >= 0.0) || !(pr.oversample >= 1.0) || pr.rank_cap < 0 || pr.sampling < 0 || pr.sampling > 2 ||
       pr.storage < 0 || pr.storage > 2)
     return IDBF_EINVAL;
@@ -970,10 +992,15 @@ extern "C" idbf_status idbf_build(const idbf_kernel* kernel, const double* x_hos
   if (!h) return IDBF_ENOMEM;
   Plan& P = h->p;
   cudaGetDevice(&P.device);
-  P.N = N; P.n0 = pr.leaf;
-  P.L = 0;
-  while ((1LL << P.L) < m) ++P.L;
+  P.N = N;
+  P.n0 = uneven ? 0 : pr.leaf;
+  P.L = L;
   P.m = (int)m; P.hV = P.L / 2; P.hU = P.L - P.hV;
+  P.uneven = uneven;
+  if (uneven) {
+    P.h_leaf_x.assign(co, co + m + 1);  // columns: the leaves of the vector x that K multiplies
+    P.h_leaf_y.assign(ro, ro + m + 1);  // rows: the leaves of y
+  }
   P.init_levels();
   idbf_status s = IDBF_OK;
   {
@@ -1019,4 +1046,46 @@ extern "C" idbf_status idbf_build(const idbf_kernel* kernel, const double* x_hos
   P.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = h;
   return P.rank_saturated > 0 ? IDBF_ERANKCAP : IDBF_OK;
+}
+
+extern "C" idbf_status idbf_build(const idbf_kernel* kernel, const double* x_host, const double* xi_host, int64_t N,
+                                  const idbf_params* params, void* stream, idbf_plan* out) {
+  if (!out) return IDBF_EINVAL;
+  *out = nullptr;
+  if (!params || params->leaf < 1 || N < 4 * (int64_t)params->leaf || N % params->leaf) return IDBF_EINVAL;
+  const int64_t m = N / params->leaf;
+  if (m & (m - 1)) return IDBF_EINVAL;
+  int L = 0;
+  while ((1LL << L) < m) ++L;
+  return build_plan(kernel, x_host, xi_host, N, L, nullptr, nullptr, params, stream, out);
+}
+
+extern "C" idbf_status idbf_build_leaves(const idbf_kernel* kernel, const double* x_host, const double* xi_host,
+                                         int64_t N, int32_t L, const int64_t* row_leaf_off,
+                                         const int64_t* col_leaf_off, const idbf_params* params, void* stream,
+                                         idbf_plan* out) {
+  if (!out) return IDBF_EINVAL;
+  *out = nullptr;
+  if (!row_leaf_off || !col_leaf_off) return IDBF_EINVAL;
+  return build_plan(kernel, x_host, xi_host, N, L, row_leaf_off, col_leaf_off, params, stream, out);
+}
+
+extern "C" idbf_status idbf_dyadic_leaves(const double* points, int64_t n, double lo, double hi, int32_t L,
+                                          int64_t* off) {
+  if (!off || n < 0 || (n > 0 && !points) || L < 0 || L > 30 || !(hi > lo)) return IDBF_EINVAL;
+  for (int64_t i = 0; i < n; ++i)
+    if (!(points[i] >= lo) || !(points[i] < hi) || (i > 0 && !(points[i] >= points[i - 1]))) return IDBF_EINVAL;
+  const int64_t m = 1LL << L;
+  // edge j = lo + (hi - lo) (j / 2^L); off[j] = number of points below edge j (binary search)
+  for (int64_t j = 0; j < m; ++j) {
+    const double edge = lo + (hi - lo) * ((double)j / (double)m);
+    int64_t a = 0, b = n;
+    while (a < b) {
+      const int64_t mid = (a + b) / 2;
+      if (points[mid] < edge) a = mid + 1; else b = mid;
+    }
+    off[j] = a;
+  }
+  off[m] = n;
+  return IDBF_OK;
 }

@@ -31,7 +31,18 @@ struct DevLevel {
   const int32_t* in_len;
   const int64_t* out_off; // boundary lev segment offsets (nullptr at lev L)
   const int32_t* out_len;
+  const int64_t* leaf;    // uneven leaves only: [m+1] offsets of the leaves of x (lev 0) or y
+                          // (lev L); nullptr for leaves of n0 points and on the inner levels
 };
+
+#ifdef __CUDACC__
+// first row and size of leaf j of the user vector read (forward level 0, adjoint level L) or
+// written (forward level L, adjoint level 0) by level d
+__device__ __forceinline__ int64_t leaf_start(const DevLevel& d, int64_t j) { return d.leaf ? d.leaf[j] : j * d.n0; }
+__device__ __forceinline__ int leaf_len(const DevLevel& d, int64_t j) {
+  return d.leaf ? (int)(d.leaf[j + 1] - d.leaf[j]) : d.n0;
+}
+#endif
 
 struct LevelInfo {
   int kind = 0;
@@ -58,6 +69,11 @@ struct Plan {
   std::vector<int64_t> h_seg_off;       // [L][2m]
   std::vector<int64_t> seg_total;       // [L]
   int64_t max_seg_total = 0;
+  // leaves of uneven size (coordinate-based trees, Example 3): offsets of the column leaves (x,
+  // read by level 0) and of the row leaves (y, written by level L); n0 = 0 then
+  bool uneven = false;
+  std::vector<int64_t> h_leaf_x, h_leaf_y;  // [m+1] each (uneven only)
+  int64_t* d_leaf = nullptr;                // device copy: x offsets, then y offsets
   int64_t mat_len = 0;                  // entries over all levels
   int64_t idx_len = 0;                  // indices over all levels
   // device: one matrix arena per level and format (offsets moff are relative to the level),
@@ -111,8 +127,11 @@ idbf_status convert_storage(Plan* p, uint32_t mask, cudaStream_t st);
 // workspace (apply.cu)
 idbf_status ensure_workspace(Plan* p, int64_t nrhs);
 
-// 3xTF32 tensor-core forward apply of all levels (apply_tc.cu); workspace must be reserved
-idbf_status apply_tf32x3(Plan* p, const void* x, void* y, int64_t R, int64_t ld, cudaStream_t st);
+// 3xTF32 tensor-core forward apply of all levels (apply_tc.cu); workspace must be reserved.
+// wide_middle: the middle factor in FP64 / double-float on the CUDA cores (apply_middle_wide).
+idbf_status apply_tf32x3(Plan* p, const void* x, void* y, int64_t R, int64_t ld, cudaStream_t st, bool wide_middle);
+// The middle factor of IDBF_MODE_TF32X3_S64 between complex64 workspace boundaries (apply.cu).
+idbf_status apply_middle_wide(Plan* p, const void* win, void* wout, int64_t R, cudaStream_t st);
 
 inline int64_t boundary_index(int b, int64_t m) { return (int64_t)b * 2 * m; }
 

@@ -181,10 +181,33 @@ struct DF64P {
   }
 };
 
+// The middle factor S^h of the split-precision tensor form (IDBF_MODE_TF32X3_S64): complex64
+// vectors on both sides, as on the tensor-core levels around it, with the products and sums in
+// FP64 (C128 storage of S^h) or in double-float (DF64 storage). Each FP32 input is exact in the
+// wider format; the output is rounded to FP32 once.
+struct FP64S32P : FP64P {
+  using vec_t = float2;
+  __device__ static __forceinline__ gv_t cvt(vec_t v) { return make_double2((double)v.x, (double)v.y); }
+  __device__ static __forceinline__ vec_t fin(const acc_t& a) { return make_float2((float)a.re, (float)a.im); }
+  __device__ static __forceinline__ vec_t add(vec_t a, vec_t b) { return make_float2(a.x + b.x, a.y + b.y); }
+  __device__ static __forceinline__ vec_t zero() { return make_float2(0.f, 0.f); }
+};
+struct DF64S32P : DF64P {
+  using vec_t = float2;
+  __device__ static __forceinline__ gv_t cvt(vec_t v) { return make_float4(v.x, 0.f, v.y, 0.f); }
+  __device__ static __forceinline__ vec_t fin(const acc_t& a) {
+    return make_float2((float)((double)a.hr + (double)a.lr), (float)((double)a.hi + (double)a.li));
+  }
+  __device__ static __forceinline__ vec_t add(vec_t a, vec_t b) { return make_float2(a.x + b.x, a.y + b.y); }
+  __device__ static __forceinline__ vec_t zero() { return make_float2(0.f, 0.f); }
+};
+
 template <class P> constexpr int fmt_of();
 template <> constexpr int fmt_of<FP64P>() { return IDBF_STORE_C128; }
 template <> constexpr int fmt_of<DF64P>() { return IDBF_STORE_DF64; }
 template <> constexpr int fmt_of<FP32P>() { return IDBF_STORE_C64; }
+template <> constexpr int fmt_of<FP64S32P>() { return IDBF_STORE_C128; }
+template <> constexpr int fmt_of<DF64S32P>() { return IDBF_STORE_DF64; }
 
 // ---------------------------------------------------------------------------------------------
 // addressing of a node's input and output segments
@@ -323,11 +346,12 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
   // phase 1: inputs -> u
   int l0, l1;
   if (d.lev == 0) {
-    l0 = d.n0;
+    l0 = leaf_len(d, j);
     l1 = 0;
+    const int64_t x0 = leaf_start(d, j);
     for (int i = tid; i < l0 * RB; i += nt) {
       const int e = i / RB, rb = i % RB;
-      u[i] = rb < nrb ? io.x[j * d.n0 + e + (int64_t)(r0 + rb) * io.ldx] : P::zero();
+      u[i] = rb < nrb ? io.x[x0 + e + (int64_t)(r0 + rb) * io.ldx] : P::zero();
     }
   } else {
     l0 = d.in_len[2 * j];
@@ -429,9 +453,10 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
   }
   __syncthreads();
   if (d.lev == d.L) {
+    const int64_t y0 = leaf_start(d, j);
     for (int i = tid; i < tl * nrb; i += nt) {
       const int e = i / nrb, rb = i % nrb;
-      io.y[j * d.n0 + e + (int64_t)(r0 + rb) * io.ldy] = t[e * RB + rb];
+      io.y[y0 + e + (int64_t)(r0 + rb) * io.ldy] = t[e * RB + rb];
     }
   } else {
     const int64_t s0 = out_seg_id(d, j, 0), s1 = out_seg_id(d, j, 1);

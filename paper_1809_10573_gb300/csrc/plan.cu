@@ -42,6 +42,7 @@ DevLevel Plan::level(int l) const {
   d.in_len = l > 0 ? d_seg_len + (l - 1) * nb : nullptr;
   d.out_off = l < L ? d_seg_off + l * nb : nullptr;
   d.out_len = l < L ? d_seg_len + l * nb : nullptr;
+  d.leaf = !uneven ? nullptr : l == 0 ? d_leaf : l == L ? d_leaf + (m + 1) : nullptr;
   return d;
 }
 
@@ -51,6 +52,7 @@ size_t Plan::device_bytes() const {
   b += nb * (2 * sizeof(int32_t) + 2 * sizeof(int64_t));
   b += (size_t)L * 2 * m * (sizeof(int32_t) + sizeof(int64_t));
   b += idx_len * sizeof(int32_t);
+  if (uneven) b += 2 * (size_t)(m + 1) * sizeof(int64_t);
   for (int f = 0; f < 3; ++f)
     for (int l = 0; l <= L && l < (int)lmat[f].size(); ++l)
       if (lmat[f][l]) b += lmat_len[l] * (f == IDBF_STORE_C64 ? 8 : 16);
@@ -92,10 +94,14 @@ idbf_status finalize_structure(Plan* p) {
     li.kmin = 1 << 30;
     for (int64_t j = 0; j < m; ++j) {
       const int64_t o = (l * m + j) * 2;
-      int in = l == 0 ? p->n0 : p->h_seg_len[(l - 1) * 2 * m + 2 * j] + p->h_seg_len[(l - 1) * 2 * m + 2 * j + 1];
+      const int leaf_x = p->uneven ? (int)(p->h_leaf_x[j + 1] - p->h_leaf_x[j]) : p->n0;
+      const int leaf_y = p->uneven ? (int)(p->h_leaf_y[j + 1] - p->h_leaf_y[j]) : p->n0;
+      int in = l == 0 ? leaf_x : p->h_seg_len[(l - 1) * 2 * m + 2 * j] + p->h_seg_len[(l - 1) * 2 * m + 2 * j + 1];
       int out = 0;
       if (l == p->L) {
-        out = p->n0;
+        out = leaf_y;
+        li.kmin = std::min(li.kmin, leaf_y);
+        li.kmax = std::max(li.kmax, leaf_y);
       } else {
         for (int c = 0; c < 2; ++c) {
           const int64_t s = (j / H) * 2 * H + j % H + c * H;
@@ -117,7 +123,7 @@ idbf_status finalize_structure(Plan* p) {
         if (li.kind == KIND_U) li.idx_entries += p->h_rows[o + c] + p->h_cols[o + c];
       }
     }
-    if (l == p->L) li.kmin = li.kmax = p->n0;
+    if (li.kmin > li.kmax) li.kmin = li.kmax;
   }
   return IDBF_OK;
 }
@@ -140,6 +146,13 @@ idbf_status upload_structure(Plan* p, cudaStream_t st) {
   IDBF_CUDA_TRY(cudaMemcpyAsync(p->d_rows, p->h_rows.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   IDBF_CUDA_TRY(cudaMemcpyAsync(p->d_cols, p->h_cols.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   IDBF_CUDA_TRY(cudaMemcpyAsync(p->d_seg_len, p->h_seg_len.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (p->uneven && !p->d_leaf) {
+    const size_t lb = 2 * (size_t)(p->m + 1) * sizeof(int64_t);
+    IDBF_CUDA_TRY(cudaMalloc((void**)&p->d_leaf, lb));
+    IDBF_CUDA_TRY(cudaMemcpyAsync(p->d_leaf, p->h_leaf_x.data(), (p->m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    IDBF_CUDA_TRY(cudaMemcpyAsync(p->d_leaf + p->m + 1, p->h_leaf_y.data(), (p->m + 1) * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice, st));
+  }
   if (!p->d_status) {
     IDBF_CUDA_TRY(cudaMalloc((void**)&p->d_status, sizeof(int)));
     IDBF_CUDA_TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
@@ -263,24 +276,52 @@ static bool is_perm(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, 
   return true;
 }
 
+// Leaf offsets of an import: both NULL (leaves of n0 points) or both valid (m + 1 entries rising
+// from 0 to N). Sets *uniform_n0 to the common leaf size when every leaf has the same positive size
+// (the uniform case, whatever way it was given), else to 0.
+static idbf_status leaf_layout(const idbf_host_factors* f, int* uniform_n0) {
+  const int64_t m = 1LL << f->L;
+  if (!f->row_leaf_off && !f->col_leaf_off) {
+    if (f->n0 < 1 || f->N != ((int64_t)f->n0 << f->L)) return IDBF_EINVAL;
+    *uniform_n0 = f->n0;
+    return IDBF_OK;
+  }
+  if (!f->row_leaf_off || !f->col_leaf_off || f->N < 1) return IDBF_EINVAL;
+  for (const int64_t* o : {f->row_leaf_off, f->col_leaf_off}) {
+    if (o[0] != 0 || o[m] != f->N) return IDBF_EINVAL;
+    for (int64_t j = 0; j < m; ++j)
+      if (o[j + 1] < o[j] || o[j + 1] - o[j] > (1 << 30)) return IDBF_EINVAL;
+  }
+  int64_t n0 = f->N / m;
+  bool same = n0 >= 1 && n0 * m == f->N;
+  for (int64_t j = 0; j < m && same; ++j)
+    same = f->row_leaf_off[j + 1] - f->row_leaf_off[j] == n0 && f->col_leaf_off[j + 1] - f->col_leaf_off[j] == n0;
+  if (same && f->n0 != 0 && f->n0 != n0) return IDBF_EINVAL;
+  *uniform_n0 = same ? (int)n0 : 0;
+  return IDBF_OK;
+}
+
 static idbf_status validate(const idbf_host_factors* f) {
   if (!f || !f->seg_len || !f->blk_rows || !f->blk_cols || !f->blk_moff || !f->blk_ioff) return IDBF_EINVAL;
-  if (f->n0 < 1 || f->L < 2 || f->L > 40) return IDBF_EINVAL;
-  if (f->N != ((int64_t)f->n0 << f->L)) return IDBF_EINVAL;
+  if (f->L < 2 || f->L > 40 || f->n0 < 0) return IDBF_EINVAL;
+  int un0 = 0;
+  const idbf_status ls = leaf_layout(f, &un0);
+  if (ls != IDBF_OK) return ls;
   if (f->mat_len < 0 || f->idx_len < 0 || (f->mat_len > 0 && !f->mat) || (f->idx_len > 0 && !f->idx)) return IDBF_EINVAL;
   const int L = f->L, hV = L / 2;
   const int64_t m = 1LL << L;
+  const int min_seg = un0 > 0 ? 1 : 0;  // uneven leaves: empty segments are allowed
   for (int64_t i = 0; i < (int64_t)L * 2 * m; ++i)
-    if (f->seg_len[i] < 1) return IDBF_EFORMAT;
+    if (f->seg_len[i] < min_seg) return IDBF_EFORMAT;
   std::vector<char> seen;
   for (int l = 0; l <= L; ++l) {
     const int kind = l < hV ? KIND_V : (l == hV ? KIND_S : KIND_U);
     const int64_t H = 1LL << (L - l);
     for (int64_t j = 0; j < m; ++j) {
       int64_t inl[2] = {0, 0}, outl[2] = {0, 0};
-      if (l == 0) inl[0] = f->n0;
+      if (l == 0) inl[0] = un0 > 0 ? un0 : f->col_leaf_off[j + 1] - f->col_leaf_off[j];
       else { inl[0] = f->seg_len[(l - 1) * 2 * m + 2 * j]; inl[1] = f->seg_len[(l - 1) * 2 * m + 2 * j + 1]; }
-      if (l == L) outl[0] = f->n0;
+      if (l == L) outl[0] = un0 > 0 ? un0 : f->row_leaf_off[j + 1] - f->row_leaf_off[j];
       else for (int c = 0; c < 2; ++c) outl[c] = f->seg_len[l * 2 * m + (j / H) * 2 * H + j % H + c * H];
       const int64_t nin = inl[0] + inl[1], nout = outl[0] + outl[1];
       for (int c = 0; c < 2; ++c) {
@@ -349,7 +390,14 @@ idbf_status idbf_import_factors(const idbf_host_factors* f, int32_t storage, voi
   if (!h) return IDBF_ENOMEM;
   Plan& p = h->p;
   cudaGetDevice(&p.device);
-  p.N = f->N; p.n0 = f->n0; p.L = f->L; p.m = 1 << f->L; p.hV = f->L / 2; p.hU = f->L - p.hV;
+  int un0 = 0;
+  leaf_layout(f, &un0);
+  p.N = f->N; p.n0 = un0; p.L = f->L; p.m = 1 << f->L; p.hV = f->L / 2; p.hU = f->L - p.hV;
+  p.uneven = un0 == 0;
+  if (p.uneven) {
+    p.h_leaf_x.assign(f->col_leaf_off, f->col_leaf_off + p.m + 1);
+    p.h_leaf_y.assign(f->row_leaf_off, f->row_leaf_off + p.m + 1);
+  }
   p.init_levels();
   const int64_t nb = (int64_t)(p.L + 1) * p.m * 2, nbl = (int64_t)p.m * 2;
   p.h_rows.assign(f->blk_rows, f->blk_rows + nb);
@@ -415,6 +463,62 @@ idbf_status idbf_set_storage(idbf_plan h, uint32_t mask, void* stream) {
   return convert_storage(&h->p, mask, (cudaStream_t)stream);
 }
 
+idbf_status idbf_clone(idbf_plan h, void* stream, idbf_plan* out) {
+  if (!h || !out) return IDBF_EINVAL;
+  *out = nullptr;
+  const Plan& a = h->p;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != a.device) return IDBF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  idbf_plan_s* c = new (std::nothrow) idbf_plan_s();
+  if (!c) return IDBF_ENOMEM;
+  Plan& b = c->p;
+  b.device = a.device;
+  b.N = a.N; b.n0 = a.n0; b.L = a.L; b.m = a.m; b.hV = a.hV; b.hU = a.hU;
+  b.init_levels();
+  b.h_rows = a.h_rows; b.h_cols = a.h_cols; b.h_moff = a.h_moff; b.h_ioff = a.h_ioff;
+  b.h_seg_len = a.h_seg_len;
+  b.uneven = a.uneven;
+  b.h_leaf_x = a.h_leaf_x;
+  b.h_leaf_y = a.h_leaf_y;
+  finalize_structure(&b);
+  b.mat_len = a.mat_len; b.idx_len = a.idx_len;
+  b.lmat_len = a.lmat_len; b.lidx_len = a.lidx_len;
+  for (int f = 0; f < 3; ++f) b.tuned[f] = a.tuned[f];
+  b.tc_split_mode = a.tc_split_mode;
+  b.wait_limit_ns = a.wait_limit_ns;
+  b.rank_saturated = a.rank_saturated;
+  b.build_seconds = 0.0;
+  idbf_status s = upload_structure(&b, st);
+  for (int l = 0; l <= a.L && s == IDBF_OK; ++l) {
+    for (int f = 0; f < 3 && s == IDBF_OK; ++f) {
+      if (!a.lmat[f][l]) continue;
+      const size_t bytes = (size_t)a.lmat_len[l] * (f == IDBF_STORE_C64 ? 8 : 16) + (f == IDBF_STORE_C64 ? 16 : 0);
+      cudaError_t e = cudaMalloc(&b.lmat[f][l], bytes);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(b.lmat[f][l], a.lmat[f][l], bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) { set_cuda_error(e); s = e == cudaErrorMemoryAllocation ? IDBF_ENOMEM : IDBF_ECUDA; }
+    }
+    if (s == IDBF_OK && a.lidx[l]) {
+      const size_t bytes = (size_t)a.lidx_len[l] * sizeof(int32_t) + 16;
+      cudaError_t e = cudaMalloc((void**)&b.lidx[l], bytes);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(b.lidx[l], a.lidx[l], bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) { set_cuda_error(e); s = e == cudaErrorMemoryAllocation ? IDBF_ENOMEM : IDBF_ECUDA; }
+    }
+  }
+  if (s == IDBF_OK) {
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { set_cuda_error(e); s = IDBF_ECUDA; }
+  }
+  if (s != IDBF_OK) { idbf_destroy(c); return s; }
+  *out = c;
+  return IDBF_OK;
+}
+
+idbf_status idbf_set_level_storage(idbf_plan h, int32_t level, uint32_t mask, void* stream) {
+  if (!h || mask == 0 || (mask & ~7u) || level < 0 || level > h->p.L) return IDBF_EINVAL;
+  return convert_level(&h->p, level, mask, (cudaStream_t)stream);
+}
+
 idbf_status idbf_sync_status(idbf_plan h, void* stream) {
   if (!h) return IDBF_EINVAL;
   Plan& p = h->p;
@@ -469,6 +573,9 @@ idbf_status idbf_stats(idbf_plan h, idbf_stats_t* s) {
   for (int f = 0; f < 3; ++f)
     for (int l = 0; l < IDBF_MAX_LEVELS; ++l)
       s->level_variant[f][l] = (l < (int)p.tuned[f].size()) ? p.tuned[f][l] : -1;
+  for (int l = 0; l <= p.L && l < IDBF_MAX_LEVELS; ++l)
+    for (int f = 0; f < 3; ++f)
+      if (p.lmat[f][l] || p.lmat_len[l] == 0) s->level_storage[l] |= 1u << f;
   return IDBF_OK;
 }
 
@@ -484,7 +591,7 @@ idbf_status idbf_save(idbf_plan h, const char* path) {
   if (!h || !path) return IDBF_EINVAL;
   const Plan& p = h->p;
   const bool have128 = p.has_format(IDBF_STORE_C128), havedf = p.has_format(IDBF_STORE_DF64);
-  if (p.mat_len > 0 && !have128 && !havedf) return IDBF_EUNSUPPORTED;
+  if ((p.mat_len > 0 && !have128 && !havedf) || p.uneven) return IDBF_EUNSUPPORTED;
   const int64_t nbl = (int64_t)p.m * 2, nb = (int64_t)(p.L + 1) * nbl;
   // file layout: global (not per-level) offsets, row-major blocks
   std::vector<int64_t> gmoff(nb), gioff(nb);
@@ -567,6 +674,7 @@ idbf_status idbf_load(const char* path, int32_t storage, void* stream, idbf_plan
   f.seg_len = seg.data(); f.blk_rows = rows.data(); f.blk_cols = cols.data();
   f.blk_moff = moff.data(); f.blk_ioff = ioff.data();
   f.mat = mat.data(); f.mat_len = hd.mat_len; f.idx = idx.data(); f.idx_len = hd.idx_len;
+  f.row_leaf_off = nullptr; f.col_leaf_off = nullptr;
   return idbf_import_factors(&f, storage, stream, out);
 }
 
@@ -581,6 +689,7 @@ void idbf_destroy(idbf_plan h) {
     for (void* q : p.lmat[f]) if (q) cudaFree(q);
   for (int32_t* q : p.lidx) if (q) cudaFree(q);
   if (p.d_meta) cudaFree(p.d_meta);
+  if (p.d_leaf) cudaFree(p.d_leaf);
   if (p.d_ws) cudaFree(p.d_ws);
   if (p.d_status) cudaFree(p.d_status);
   if (cur != p.device) cudaSetDevice(cur);

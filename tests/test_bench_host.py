@@ -82,3 +82,33 @@ def test_level_variants_option_parsing():
     assert bench.parse_level_variants(" df64=7,1 ; fp32=3,15 ;") == {"df64": [7, 1], "fp32": [3, 15]}
     with pytest.raises(ValueError):
         bench.parse_level_variants("df64=7,x")
+
+
+def test_oracle_team_times_one_core_then_all(monkeypatch):
+    """The CPU baseline's worker processes (spawned: no CUDA state is inherited) build the oracle's
+    factorization, then run the single-core and the all-core phases in lockstep with the parent."""
+    team = bench.OracleTeam(2, 9, steps_single=2, steps_all=3)
+    try:
+        times = team.run()
+    finally:
+        team.close()
+    assert [len(t) for t in times] == [2, 3] and all(v > 0 for t in times for v in t)
+    assert team.entries > 0
+    cb = bench.cpu_summary(team, times, 100 * team.entries)
+    assert cb["cores"] == 2 and cb["kind"] == "oracle" and cb["single_core"]["cores"] == 1
+    # two processes each applying once per step, entries scaled by 100
+    assert abs(cb["value"] - 2 / (sorted(times[1])[1] * 100)) < 1e-9 * cb["value"]
+
+
+def test_reference_arm_prints_one_measured_line(monkeypatch, capsys):
+    import argparse
+    import json
+    monkeypatch.setattr(bench, "CPU_LOG2", 9)
+    monkeypatch.setattr(bench, "host_cores", lambda: 2)
+    args = argparse.Namespace(gpus=1, steps=3, warmup=3)
+    assert bench.cpu_arm(args, 0, 1) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["cpu_baseline"]["cores"] == 2
+    # ms_per_step is the wall time a step really took: the timed steps fit the run
+    assert line["ms_per_step"] * line["steps"] < 60e3
+    assert line["e2e"]["value"] == line["value"]

@@ -144,3 +144,21 @@ def test_cuda_j0_entries_match_the_host_routine():
     assert np.all(np.abs(got - ref) <= bound)
     assert rel(got, ref) < 1e-11
 
+
+
+def test_clone_is_an_independent_bitwise_copy():
+    """idbf_clone copies every factor, index list and storage format: the clone's applies equal
+    the original's bit for bit in every mode it holds, and survive the original's destruction."""
+    N, n0 = 2048, 16
+    x, xi = inputs.jittered_grid(N, seed=N)
+    plan = P.Plan.build(x, xi, eps=1e-6, leaf=n0, kernel="dft", sign=-1)
+    plan.set_storage(P.STORE_C128, P.STORE_DF64, P.STORE_C64)
+    g = torch.from_numpy(inputs.complex_gaussian(N, 3, seed=9)).cuda()
+    want = {m: plan.apply(g if m != P.MODE_FP32 else g.to(torch.complex64), mode=m).cpu()
+            for m in (P.MODE_FP64, P.MODE_DF64, P.MODE_FP32)}
+    twin = plan.clone()
+    assert twin.stats()["level_storage"] == plan.stats()["level_storage"]
+    plan.close()
+    for m, y in want.items():
+        got = twin.apply(g if m != P.MODE_FP32 else g.to(torch.complex64), mode=m).cpu()
+        assert torch.equal(got, y), m

@@ -1,10 +1,16 @@
 """The 3xTF32 tensor-core apply (tcgen05) of many right-hand sides against the oracle.
 
 Split precision: every FP32 operand is x_hi + x_lo with x_hi = tf32(x); the three products
-hi*hi + hi*lo + lo*hi accumulate in FP32, so a block product is as accurate as an FP32 one
-(unit roundoff 6e-8, plus ~2^-22 from the lo parts held in TF32). Through L + 1 levels of sums of a
-few hundred terms that bounds the error against the oracle's FP64 apply of the same factors by
-~1e-5; the test uses 2e-5, the same bar as the FP32 CUDA-core apply."""
+hi*hi + hi*lo + lo*hi accumulate in FP32, so a block product is about as accurate as an FP32
+one. The bar is the one stated for the split-FP32 tensor form: relative 2-norm error at most
+eps + 1e-6 against the oracle's FP64 apply of the same factors (the factorization error eps does
+not even enter this comparison, so the bar is met with eps to spare). Cases: eps = 1e-6 FIO
+(Example 1 kernel of the benchmark) at N = 8192 with blocks of up to 162 rows (three 64-row
+passes of the tensor-core tile), full 128-RHS tiles and ragged ones, the jittered DFT and the
+paper's FIO at eps = 1e-6, and two eps = 1e-8 cases.
+
+IDBF_MODE_TF32X3_S64 applies the middle factor S^h in double-float or FP64 on the CUDA cores
+(complex64 vectors on its two sides) and every other level as above; it meets the same bar."""
 import numpy as np
 import pytest
 import torch
@@ -27,8 +33,12 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
-@pytest.mark.parametrize("case,nrhs", [("dft_1024", 5), ("dft_1024", 130), ("fio_base_4096", 256),
-                                       ("fio_base_8192_oddL", 64), ("fio_paper_2048", 17)])
+CASES_TC = [("fio_base_8192_oddL", 256), ("fio_base_8192_oddL", 61), ("fio_base_8192_oddL", 160),
+            ("dft_jit_2048_oddL", 256), ("fio_paper_2048", 130), ("fio_base_4096", 256), ("dft_1024", 5),
+            ("dft_1024", 130)]
+
+
+@pytest.mark.parametrize("case,nrhs", CASES_TC)
 def test_tf32x3_matches_oracle(case, nrhs):
     c = oracle_case(case)
     plan = P.Plan.import_factors(c["ex"], storage=P.STORE_C64)
@@ -38,8 +48,40 @@ def test_tf32x3_matches_oracle(case, nrhs):
     plan.sync_status()
     ref = idbf.apply(c["F"], X)
     e_tc = rel(y.cpu().numpy(), ref)
-    e_32 = rel(plan.apply(xd, mode=P.MODE_FP32).cpu().numpy(), ref)
-    assert e_tc < 2e-5, (e_tc, e_32)
+    assert e_tc <= c["eps"] + 1e-6, e_tc
+
+
+@pytest.mark.parametrize("middle", [P.STORE_DF64, P.STORE_C128], ids=["df64", "fp64"])
+@pytest.mark.parametrize("case,nrhs", [("fio_base_8192_oddL", 256), ("fio_base_8192_oddL", 61),
+                                       ("dft_jit_2048_oddL", 130), ("fio_paper_2048", 7)])
+def test_tf32x3_with_a_wide_middle_factor_matches_oracle(case, nrhs, middle):
+    c = oracle_case(case)
+    plan = P.Plan.import_factors(c["ex"], storage=P.STORE_C128)
+    plan.set_storage(P.STORE_C128, P.STORE_C64)
+    hv = plan.L // 2
+    for l in range(plan.L + 1):   # C64 everywhere, the wide format only on the middle level
+        plan.set_level_storage(l, *((middle, P.STORE_C64) if l == hv else (P.STORE_C64,)))
+    st = plan.stats()
+    held = [v for v, e in zip(st["level_storage"], st["level_entries"]) if e > 0]   # empty levels hold every format
+    assert st["level_storage"][hv] == (1 << middle) | (1 << P.STORE_C64)
+    assert sorted(held).count(1 << P.STORE_C64) == len(held) - 1
+    X = inputs.complex_gaussian(c["N"], nrhs, seed=83)
+    xd = torch.from_numpy(X.astype(np.complex64)).cuda()
+    y = plan.apply(xd, mode=P.MODE_TF32X3_S64)
+    plan.sync_status()
+    ref = idbf.apply(c["F"], X)
+    assert rel(y.cpu().numpy(), ref) <= c["eps"] + 1e-6
+    # the mode of the wide format alone is refused: the other levels do not hold it
+    with pytest.raises(P.IDBFError):
+        plan.apply(xd.to(torch.complex128), mode=P.MODE_FP64 if middle == P.STORE_C128 else P.MODE_DF64)
+
+
+def test_wide_middle_needs_a_wide_middle_level():
+    c = oracle_case("dft_1024")
+    plan = P.Plan.import_factors(c["ex"], storage=P.STORE_C64)
+    xd = torch.zeros((c["N"], 2), dtype=torch.complex64, device="cuda")
+    with pytest.raises(P.IDBFError):
+        plan.apply(xd, mode=P.MODE_TF32X3_S64)
 
 
 def test_tf32x3_adjoint_is_refused():
@@ -66,3 +108,6 @@ def test_tf32x3_tall_blocks_within_the_split_precision_bar():
     plan.sync_status()
     err = rel(ytc.cpu().numpy(), y64)
     assert err < 2e-6, err
+    yw = plan.apply(torch.from_numpy(X.astype(np.complex64)).cuda(), mode=P.MODE_TF32X3_S64)
+    plan.sync_status()
+    assert rel(yw.cpu().numpy(), y64) < 2e-6
