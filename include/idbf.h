@@ -244,18 +244,25 @@ idbf_status idbf_apply_noalloc(idbf_plan plan, const void* x, void* y, int64_t n
  * the consumers; 7: one warp per node, for levels of short blocks; 8-13: 1-6 with the columns
  * of blocks of at most 96 rows split between up to four thread groups, whose partial sums are
  * added at the end; 14-15: a fourth ring layout with four CTAs per SM and small stages, for
- * levels of short blocks, with the split) `reps` times with CUDA events on `stream`, and keep
- * the fastest per level in the
- * plan (idbf_stats reports them). Later idbf_apply calls use the choices; results are identical
- * up to the summation order of the double-float / FP32 partial sums. Synchronous; allocates two
- * N-vector temporaries. *apply_ms (if not NULL) receives the summed best level times.
+ * levels of short blocks, with the split; 16-19: levels l and l + 1 fused in one launch of the
+ * streaming kernel, ring layouts A-D: each CTA takes two nodes of level l and the two nodes of
+ * level l + 1 that read their four output segments, which stay in shared memory, the radix-2
+ * case of level fusion) `reps` times with CUDA events on `stream`, and keep the cheapest cover
+ * of the levels by single levels and fused pairs in the plan (idbf_stats reports the variant of
+ * every level; both levels of a fused pair report the pair's variant). Later idbf_apply calls
+ * use the choices; results are identical up to the summation order of the double-float / FP32
+ * partial sums. Synchronous; allocates two N-vector temporaries. *apply_ms (if not NULL)
+ * receives the summed best times. FP64 runs variants 0 and 7 only.
  * Errors: EINVAL, EUNSUPPORTED (storage for `mode` absent), ENOMEM, ECUDA. */
 idbf_status idbf_autotune(idbf_plan plan, int32_t mode, int32_t reps, void* stream, float* apply_ms);
 
 /* idbf_set_level_variants - set the forward kernel variant of every level for `mode` directly
- * (n = L + 1 values in 0..IDBF_NUM_FWD_VARIANTS-1, -1 = default; n = 0 clears), e.g. to restore the choices of an
- * earlier idbf_autotune. A variant that does not fit a level falls back to variant 0. */
-#define IDBF_NUM_FWD_VARIANTS 16
+ * (n = L + 1 values in 0..IDBF_NUM_FWD_VARIANTS-1, -1 = default; n = 0 clears), e.g. to restore the
+ * choices of an earlier idbf_autotune. Levels are read from 0 upwards: a pair variant (16-19) on
+ * level l covers levels l and l + 1 (the entry of level l + 1 is then not read); on level L it
+ * runs level L alone. A variant that does not fit a level falls back to the default, then to
+ * variant 0. */
+#define IDBF_NUM_FWD_VARIANTS 20
 idbf_status idbf_set_level_variants(idbf_plan plan, int32_t mode, const int32_t* variants, int32_t n);
 
 /* idbf_set_tc_split - operand splitting of the 3xTF32 tensor-core mode: 0 = x_hi + x_lo with

@@ -16,7 +16,7 @@ KERNEL_FIO1D, KERNEL_DFT, KERNEL_J0 = 0, 1, 2
 SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, SAMPLE_ALL = 0, 1, 2
 STORE_C128, STORE_DF64, STORE_C64 = 0, 1, 2
 MODE_FP64, MODE_DF64, MODE_FP32, MODE_TF32X3, MODE_TF32X3_S64 = 0, 1, 2, 3, 4
-NUM_FWD_VARIANTS = 16  # IDBF_NUM_FWD_VARIANTS
+NUM_FWD_VARIANTS = 20  # IDBF_NUM_FWD_VARIANTS
 MAX_LEVELS = 48
 NOALLOC_SCRATCH_BYTES = 64 << 20
 

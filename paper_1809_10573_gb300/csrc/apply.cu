@@ -296,11 +296,13 @@ __host__ __device__ __forceinline__ int cols_per_chunk(int rows, int es, int sta
 // node without a global-memory round trip.
 struct NodeMeta {
   int64_t in0, io[2], mo[2], ob[2];
+  int64_t j;  // node index on its level
   int l0, l1, rows[2], cols[2], olen0;
+  int sel;    // level pairs: 0 = the first level (outputs to shared memory), 1 = the second
 };
 
 struct Geo {
-  size_t vec_off, ibuf_off, g_off, t_off, red_off, bar_off, total;
+  size_t vec_off, ibuf_off, g_off, t_off, red_off, mid_off, bar_off, total;
   int ucap, icap;  // elements of one input buffer, ints of one index buffer
 };
 // Shared memory: the stage ring, two input buffers (node inputs, copied by the producer), two
@@ -308,7 +310,8 @@ struct Geo {
 // the reduction buffer and the mbarriers. The reduction buffer holds one partial sum per thread of
 // teams 1.. (and, with the column split, of team 0 too).
 template <class P, class RG>
-__host__ __device__ inline Geo geometry(int max_in, int max_out, int max_cols_pair, int rpt, int split) {
+__host__ __device__ inline Geo geometry(int max_in, int max_out, int max_cols_pair, int rpt, int split,
+                                        int mid_elems = 0) {
   using V = typename P::vec_t;
   using G = typename P::gv_t;
   constexpr int STAGES = RG::STAGES, STAGE_BYTES = RG::STAGE_BYTES;
@@ -324,16 +327,24 @@ __host__ __device__ inline Geo geometry(int max_in, int max_out, int max_cols_pa
   q.t_off = q.g_off + (((size_t)gsz * sizeof(G) + 127) & ~(size_t)127);
   q.red_off = q.t_off + (((size_t)max_out * sizeof(V) + 127) & ~(size_t)127);
   const int slots = split ? RG::TEAMS : (RG::TEAMS > 1 ? RG::TEAMS - 1 : 1);
-  q.bar_off = q.red_off + (((size_t)slots * rpt * TCT * sizeof(typename P::part_t) + 127) & ~(size_t)127);
+  q.mid_off = q.red_off + (((size_t)slots * rpt * TCT * sizeof(typename P::part_t) + 127) & ~(size_t)127);
+  q.bar_off = q.mid_off + (((size_t)mid_elems * sizeof(V) + 127) & ~(size_t)127);
   q.total = q.bar_off + 4 * STAGES * sizeof(uint64_t);
   return q;
 }
 }  // namespace strm
 
-template <class P, class RG, int RPT, bool SPLIT>
+// PAIR: the launch runs two consecutive levels l (d, mat) and l + 1 (d1, mat1) as a radix-2
+// fusion (the closed groups of Eq. expressUSV, as in an FFT): work unit u is the group of level-l
+// nodes j0 = aH + r and j0 + 1 (H = 2^(L-l), r = 2 (u mod H/2), a = u div H/2), whose four
+// output segments are exactly the inputs of level-(l+1) nodes aH + r/2 and aH + r/2 + H/2. The
+// four segments stay in shared memory (mid): level l writes them there, level l + 1 reads them
+// there; boundary l never reaches global memory. Without PAIR a unit is one node of level l.
+template <class P, class RG, int RPT, bool SPLIT, bool PAIR>
 __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
-    k_level_stream(DevLevel d, const typename P::mat_t* __restrict__ mat, IO<typename P::vec_t> io, int max_in,
-                   int max_out, int max_cols_pair, int x_bulk, int* __restrict__ status, uint64_t limit_ns,
+    k_level_stream(DevLevel d, const typename P::mat_t* __restrict__ mat, DevLevel d1,
+                   const typename P::mat_t* __restrict__ mat1, IO<typename P::vec_t> io, int max_in, int max_out,
+                   int max_cols_pair, int mid_elems, int x_bulk, int* __restrict__ status, uint64_t limit_ns,
                    int producer_enabled) {
   using namespace strm;
   using V = typename P::vec_t;
@@ -343,15 +354,17 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
   constexpr int VS = (int)sizeof(V);
   constexpr int STAGES = RG::STAGES, STAGE_BYTES = RG::STAGE_BYTES;
   constexpr int TEAMS = RG::TEAMS, NCT = RG::NCT;
+  constexpr int NSUB = PAIR ? 4 : 1;  // nodes per work unit
   extern __shared__ __align__(128) unsigned char smem[];
   static_assert(RPT == 1 || !SPLIT, "the column split is for one output row per thread");
-  const Geo geo = geometry<P, RG>(max_in, max_out, max_cols_pair, RPT, SPLIT);
+  const Geo geo = geometry<P, RG>(max_in, max_out, max_cols_pair, RPT, SPLIT, PAIR ? mid_elems : 0);
   unsigned char* stages = smem;
   V* ubuf = (V*)(smem + geo.vec_off);              // [2][ucap]
   int32_t* ibuf = (int32_t*)(smem + geo.ibuf_off);  // [2][icap]
   G* g = (G*)(smem + geo.g_off);
   V* t = (V*)(smem + geo.t_off);
   typename P::part_t* red = (typename P::part_t*)(smem + geo.red_off);
+  V* mid = (V*)(smem + geo.mid_off);                // level pairs: the four shared segments
   uint64_t* full = (uint64_t*)(smem + geo.bar_off);
   uint64_t* empty = full + STAGES;
   uint64_t* in_full = empty + STAGES;   // [2]
@@ -362,6 +375,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
   __shared__ int cons_abort;
   __shared__ NodeMeta nmeta[2];  // description of the node in input buffer b
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nunits = PAIR ? d.m / 2 : d.m;
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(&full[i], 1);
@@ -383,41 +397,73 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     if (lane != 0) return;
     uint32_t it = 0, nn = 0;
     bool ok = true;
-    // node descriptions are loaded one node ahead, so that no copy waits for them
-    auto meta = [&](int64_t jj) {
+    // node description of node jj on level dl; outputs to global memory
+    auto meta_of = [&](const DevLevel& dl, int64_t jj) {
       NodeMeta m;
-      m.in0 = d.lev == 0 ? 0 : d.in_off[2 * jj];
-      m.l0 = d.lev == 0 ? d.n0 : d.in_len[2 * jj];
-      m.l1 = d.lev == 0 ? 0 : d.in_len[2 * jj + 1];
+      m.j = jj;
+      m.sel = 0;
+      m.in0 = dl.lev == 0 ? 0 : dl.in_off[2 * jj];
+      m.l0 = dl.lev == 0 ? dl.n0 : dl.in_len[2 * jj];
+      m.l1 = dl.lev == 0 ? 0 : dl.in_len[2 * jj + 1];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        m.io[c] = d.ioff[2 * jj + c];
-        m.mo[c] = d.moff[2 * jj + c];
-        m.rows[c] = d.rows[2 * jj + c];
-        m.cols[c] = d.cols[2 * jj + c];
+        m.io[c] = dl.ioff[2 * jj + c];
+        m.mo[c] = dl.moff[2 * jj + c];
+        m.rows[c] = dl.rows[2 * jj + c];
+        m.cols[c] = dl.cols[2 * jj + c];
       }
       m.ob[0] = m.ob[1] = 0;
       m.olen0 = 0;
-      if (d.lev < d.L) {
-        const int64_t s0 = out_seg_id(d, jj, 0), s1 = out_seg_id(d, jj, 1);
-        m.ob[0] = d.out_off[s0];
-        m.ob[1] = d.out_off[s1];
-        m.olen0 = d.out_len[s0];
+      if (dl.lev < dl.L) {
+        const int64_t s0 = out_seg_id(dl, jj, 0), s1 = out_seg_id(dl, jj, 1);
+        m.ob[0] = dl.out_off[s0];
+        m.ob[1] = dl.out_off[s1];
+        m.olen0 = dl.out_len[s0];
       }
       return m;
     };
-    NodeMeta nxt = meta(blockIdx.x < d.m ? (int64_t)blockIdx.x : 0);
-    for (int64_t j = blockIdx.x; j < d.m && ok; j += gridDim.x, ++nn) {
+    // node v of work unit un (node descriptions are loaded one node ahead, so that no copy
+    // waits for them); for level pairs the shared-memory offsets replace the segment offsets
+    auto meta = [&](int64_t un, int v) {
+      if (!PAIR) return meta_of(d, un);
+      const int64_t hh = (int64_t)d.H >> 1, a = un / hh, r = 2 * (un % hh);
+      const int64_t sA = a * 2 * d.H + r, sB = sA + d.H;  // segments of level l written by j0, j0 + 1
+      const int lA0 = d.out_len[sA], lA1 = d.out_len[sA + 1], lB0 = d.out_len[sB];
+      NodeMeta m;
+      if (v < 2) {
+        m = meta_of(d, a * d.H + r + v);
+        m.ob[0] = v == 0 ? 0 : lA0;
+        m.ob[1] = v == 0 ? lA0 + lA1 : lA0 + lA1 + lB0;
+      } else {
+        m = meta_of(d1, a * d.H + (r >> 1) + (v - 2) * hh);
+        m.in0 = v == 2 ? 0 : lA0 + lA1;
+        m.sel = 1;
+      }
+      return m;
+    };
+    int64_t un = blockIdx.x;
+    int v = 0;
+    NodeMeta nxt = meta(un < nunits ? un : 0, 0);
+    for (; un < nunits && ok; ++nn) {
       const NodeMeta cur = nxt;
-      if (j + gridDim.x < d.m) nxt = meta(j + gridDim.x);
+      const int64_t j = cur.j;
+      const bool second = PAIR && cur.sel;
+      const DevLevel& dl = second ? d1 : d;
+      const typename P::mat_t* ml = second ? mat1 : mat;
+      // the next node: the next of this unit, else the first of the next unit
+      if (v + 1 < NSUB) ++v;
+      else { v = 0; un += gridDim.x; }
+      if (un < nunits) nxt = meta(un, v);
       // node inputs and index lists into buffer nn & 1 (released by the consumers of node nn-2)
       const int b = nn & 1;
       if (!wait_bounded(&in_empty[b], ((nn >> 1) & 1) ^ 1, limit_ns, &abort_flag)) { ok = false; break; }
-      const unsigned char* usrc;
+      const unsigned char* usrc = nullptr;
       uint32_t ubytes = 0;
-      if (d.lev == 0) {
-        usrc = (const unsigned char*)(io.x + j * d.n0);
-        ubytes = inputs_bulk ? (uint32_t)(d.n0 * VS) : 0;
+      if (second) {
+        // inputs already in shared memory (mid)
+      } else if (dl.lev == 0) {
+        usrc = (const unsigned char*)(io.x + j * dl.n0);
+        ubytes = inputs_bulk ? (uint32_t)(dl.n0 * VS) : 0;
       } else {
         usrc = (const unsigned char*)(io.win + cur.in0);
         ubytes = inputs_bulk ? (uint32_t)((cur.l0 + cur.l1) * VS) : 0;
@@ -426,9 +472,9 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       const uint32_t ucopy = ubytes ? (uint32_t)((((uintptr_t)usrc + ubytes + 15) & ~(uintptr_t)15) - (uintptr_t)ua) : 0;
       uint32_t icopy[2] = {0, 0};
       const unsigned char* ia[2] = {nullptr, nullptr};
-      if (d.kind != KIND_S && inputs_bulk) {
+      if (dl.kind != KIND_S && inputs_bulk) {
         for (int c = 0; c < 2; ++c) {
-          const unsigned char* is = (const unsigned char*)(d.idx + cur.io[c]);
+          const unsigned char* is = (const unsigned char*)(dl.idx + cur.io[c]);
           const uint32_t ib = (uint32_t)((cur.rows[c] + cur.cols[c]) * 4);
           ia[c] = (const unsigned char*)((uintptr_t)is & ~(uintptr_t)15);
           icopy[c] = (uint32_t)((((uintptr_t)is + ib + 15) & ~(uintptr_t)15) - (uintptr_t)ia[c]);
@@ -447,7 +493,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
         const int rows = cur.rows[c], cols = cur.cols[c];
         if (rows == 0 || cols == 0) continue;
         const int cpc = cols_per_chunk(rows, ES, STAGE_BYTES);
-        const unsigned char* base = (const unsigned char*)(mat + cur.mo[c]);
+        const unsigned char* base = (const unsigned char*)(ml + cur.mo[c]);
         for (int j0 = 0; j0 < cols; j0 += cpc, ++it) {
           const int nc = min(cpc, cols - j0);
           const int stg = it % STAGES;
@@ -485,7 +531,8 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
   const int tr = tc - team * TCT;       // row index within the team
   uint32_t it = 0, nn = 0;
   bool failed = false;
-  for (int64_t j = blockIdx.x; j < d.m; j += gridDim.x, ++nn) {
+  for (int64_t un = blockIdx.x; un < nunits; un += gridDim.x) {
+  for (int sub = 0; sub < NSUB; ++sub, ++nn) {
     consumer_sync<NCT>();
     if (*(volatile int*)&cons_abort) break;
     const int b = nn & 1;
@@ -493,42 +540,53 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     // the node's description from the producer (acquired by the wait above); after a failed wait
     // it may be incomplete, so every size is zero and the loops below do nothing
     const NodeMeta& nm = nmeta[b];
+    const bool second = PAIR && sub >= 2;   // level l + 1 of a pair: inputs from mid
+    const bool to_mid = PAIR && sub < 2;    // level l of a pair: outputs to mid
+    const int kind = second ? d1.kind : d.kind;
+    const int lev = second ? d1.lev : d.lev;
+    const int Lv = d.L, n0 = d.n0;
+    const int32_t* lidx = second ? d1.idx : d.idx;
+    const int64_t j = nm.j;
     const int l0 = failed ? 0 : nm.l0, l1 = failed ? 0 : nm.l1;
     const int rows0 = failed ? 0 : nm.rows[0], rows1 = failed ? 0 : nm.rows[1];
     const int cols0 = failed ? 0 : nm.cols[0], cols1 = failed ? 0 : nm.cols[1];
     const int64_t obv[2] = {nm.ob[0], nm.ob[1]};
     const int olen0 = failed ? 0 : nm.olen0;
     const int64_t in0 = nm.in0;
-    const int64_t iov[2] = {d.kind != KIND_S ? nm.io[0] : 0, d.kind != KIND_S ? nm.io[1] : 0};
+    const int64_t iov[2] = {kind != KIND_S ? nm.io[0] : 0, kind != KIND_S ? nm.io[1] : 0};
     const int64_t mov[2] = {nm.mo[0], nm.mo[1]};
+    const M* ml = second ? mat1 : mat;
+    V* const outp = to_mid ? mid : io.wout;  // where this node's output segments go
     // inputs (shifted within 16 bytes of the copy) and index lists in shared memory
     const V* u;
-    {
-      const uintptr_t usrc = d.lev == 0 ? (uintptr_t)(io.x + j * d.n0) : (uintptr_t)(io.win + in0);
+    if (second) {
+      u = mid + in0;
+    } else {
+      const uintptr_t usrc = lev == 0 ? (uintptr_t)(io.x + j * n0) : (uintptr_t)(io.win + in0);
       u = ubuf + (size_t)b * geo.ucap + (int)((usrc & 15) / VS);
-    }
-    if (!inputs_bulk) {  // plain loads by the consumers
-      V* uw = ubuf + (size_t)b * geo.ucap;
-      if (d.lev == 0) {
-        for (int i = tc; i < l0; i += NCT) uw[i] = io.x[j * d.n0 + i];
-      } else {
-        const V* src = io.win + in0;
-        for (int i = tc; i < l0 + l1; i += NCT) uw[i] = src[i];
+      if (!inputs_bulk) {  // plain loads by the consumers
+        V* uw = ubuf + (size_t)b * geo.ucap;
+        if (lev == 0) {
+          for (int i = tc; i < l0; i += NCT) uw[i] = io.x[j * n0 + i];
+        } else {
+          const V* src = io.win + in0;
+          for (int i = tc; i < l0 + l1; i += NCT) uw[i] = src[i];
+        }
+        u = uw;
       }
-      u = uw;
     }
     const int32_t* ix0 = nullptr;
     const int32_t* ix1 = nullptr;
-    if (d.kind != KIND_S) {
+    if (kind != KIND_S) {
       int32_t* ib0 = ibuf + (size_t)b * geo.icap;
       if (inputs_bulk) {
-        const uintptr_t s0 = (uintptr_t)(d.idx + iov[0]), s1 = (uintptr_t)(d.idx + iov[1]);
+        const uintptr_t s0 = (uintptr_t)(lidx + iov[0]), s1 = (uintptr_t)(lidx + iov[1]);
         const uint32_t c0 = (uint32_t)((((s0 + (rows0 + cols0) * 4 + 15) & ~(uintptr_t)15)) - (s0 & ~(uintptr_t)15));
         ix0 = ib0 + (int)((s0 & 15) / 4);
         ix1 = ib0 + ((c0 / 4 + 3) & ~3) + (int)((s1 & 15) / 4);
       } else {
-        const int32_t* g0 = d.idx + iov[0];
-        const int32_t* g1 = d.idx + iov[1];
+        const int32_t* g0 = lidx + iov[0];
+        const int32_t* g1 = lidx + iov[1];
         for (int i = tc; i < rows0 + cols0; i += NCT) ib0[i] = g0[i];
         for (int i = tc; i < rows1 + cols1; i += NCT) ib0[rows0 + cols0 + i] = g1[i];
         ix0 = ib0;
@@ -538,13 +596,13 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     consumer_sync<NCT>();
     // gathered operands: V: g = [u[p_0], u[p_1]]; S and U: g = u
     if (!failed) {
-      if (d.kind == KIND_V) {
+      if (kind == KIND_V) {
         for (int i = tc; i < cols0; i += NCT) g[i] = P::cvt(u[ix0[rows0 + i]]);
         for (int i = tc; i < cols1; i += NCT) g[cols0 + i] = P::cvt(u[ix1[rows1 + i]]);
       } else {
         for (int i = tc; i < l0 + l1; i += NCT) g[i] = P::cvt(u[i]);
       }
-      if (d.kind == KIND_U)  // t[q_0] = in_0; t[p_0] comes from the block-0 products
+      if (kind == KIND_U)  // t[q_0] = in_0; t[p_0] comes from the block-0 products
         for (int i = tc; i < l0; i += NCT) t[ix0[i]] = u[i];
     }
     consumer_sync<NCT>();
@@ -552,8 +610,8 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     for (int c = 0; c < 2; ++c) {
       const int rows = c ? rows1 : rows0, cols = c ? cols1 : cols0;
       const int32_t* ix = c ? ix1 : ix0;
-      const G* gc = g + (d.kind == KIND_S ? 0 : (d.kind == KIND_V ? c * cols0 : c * l0));
-      if (d.kind == KIND_U && c == 1 && !failed) {  // block 0 has written all of t
+      const G* gc = g + (kind == KIND_S ? 0 : (kind == KIND_V ? c * cols0 : c * l0));
+      if (kind == KIND_U && c == 1 && !failed) {  // block 0 has written all of t
         for (int i = tc; i < l1; i += NCT) { V* q = &t[ix1[i]]; *q = P::add(*q, u[l0 + i]); }
       }
       typename P::acc_t acc[RPT];
@@ -566,7 +624,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       const int rr = tr - grp * rows;
       if (work) {
         const int cpc = cols_per_chunk(rows, ES, STAGE_BYTES);
-        const uintptr_t base = (uintptr_t)(mat + mov[c]);
+        const uintptr_t base = (uintptr_t)(ml + mov[c]);
         const uint32_t chunk_bytes = (uint32_t)cpc * rows * ES;
         int since = 0;
         uintptr_t src = base;
@@ -637,16 +695,16 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
               P::combine(acc[k], red[((SPLIT ? tm : tm - 1) * RPT + k) * TCT + tr]);
           }
           const V v = P::fin(acc[k]);
-          if (d.kind == KIND_U) {
+          if (kind == KIND_U) {
             V* q = &t[ix[(c ? l1 : l0) + r]];
             *q = c ? P::add(*q, v) : v;
           } else {
-            io.wout[ob + r] = d.kind == KIND_V ? P::add(v, u[ix[r]]) : v;
+            outp[ob + r] = kind == KIND_V ? P::add(v, u[ix[r]]) : v;
           }
         }
       }
-      if (d.kind == KIND_V && cols == 0 && !failed) {  // all skeleton: out = u[q]
-        for (int r = tc; r < rows; r += NCT) io.wout[ob + r] = u[ix[r]];
+      if (kind == KIND_V && cols == 0 && !failed) {  // all skeleton: out = u[q]
+        for (int r = tc; r < rows; r += NCT) outp[ob + r] = u[ix[r]];
       }
       consumer_sync<NCT>();  // red is reused by the next block; t must be complete before c = 1
     }
@@ -657,15 +715,17 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       abort_flag = 1;
       cons_abort = 1;
     }
-    if (d.kind == KIND_U) {
+    if (kind == KIND_U) {
       consumer_sync<NCT>();
       if (*(volatile int*)&cons_abort) break;
-      if (d.lev == d.L) {
-        for (int i = tc; i < tl; i += NCT) io.y[j * d.n0 + i] = t[i];
+      if (lev == Lv) {
+        for (int i = tc; i < tl; i += NCT) io.y[j * n0 + i] = t[i];
       } else {
-        for (int i = tc; i < tl; i += NCT) io.wout[i < olen0 ? obv[0] + i : obv[1] + (i - olen0)] = t[i];
+        for (int i = tc; i < tl; i += NCT) outp[i < olen0 ? obv[0] + i : obv[1] + (i - olen0)] = t[i];
       }
     }
+  }
+  if (*(volatile int*)&cons_abort) break;
   }
 }
 
@@ -696,45 +756,69 @@ __global__ void __launch_bounds__(kWarpNodeWarps * 32) k_level_warp(DevLevel d, 
 // variants 14, 15: ring layout D (four CTAs per SM) with the column split, inputs copied by the
 // producer or loaded by the consumers.
 constexpr int kNumFwdVariants = IDBF_NUM_FWD_VARIANTS;
+// variants kFirstPairVariant .. + 3 on level l run levels l and l + 1 in one launch (radix-2
+// level fusion; streaming kernel with ring layout A, B, C or D, inputs copied by the producer,
+// column split of short blocks)
+constexpr int kFirstPairVariant = 16;
+static_assert(kFirstPairVariant + 4 == kNumFwdVariants, "pair variants close the list");
+static bool is_pair_variant(int v) { return v >= kFirstPairVariant && v < kNumFwdVariants; }
 
 static int default_variant(int fmt) { return fmt == IDBF_STORE_C128 ? 0 : 1; }
 
+// One level l (pair = false) or the fused pair of levels l, l + 1 (pair = true) with the
+// streaming kernel and ring layout RG.
 template <class P, class RG>
-static idbf_status launch_stream(Plan* p, int l, bool bulk, bool split_short, const void* x, IO<typename P::vec_t> io,
-                                 cudaStream_t st) {
+static idbf_status launch_stream(Plan* p, int l, bool pair, bool bulk, bool split_short, const void* x,
+                                 IO<typename P::vec_t> io, cudaStream_t st) {
   using V = typename P::vec_t;
+  if (pair && (l + 1 > p->L)) return IDBF_EUNSUPPORTED;
   const LevelInfo& li = p->lv[l];
-  if (!p->d_status || li.max_rows > strm::MAX_RPT * strm::TCT ||
-      li.max_rows * (int)sizeof(typename P::mat_t) > RG::STAGE_BYTES - 32)
+  const LevelInfo& lj = p->lv[pair ? l + 1 : l];
+  const int max_rows = std::max(li.max_rows, lj.max_rows);
+  if (!p->d_status || max_rows > strm::MAX_RPT * strm::TCT ||
+      max_rows * (int)sizeof(typename P::mat_t) > RG::STAGE_BYTES - 32)
     return IDBF_EUNSUPPORTED;
-  const int rpt = li.max_rows <= strm::TCT ? 1 : 2;
+  const int max_in = std::max(li.max_in, lj.max_in), max_out = std::max(li.max_out, lj.max_out);
+  const int max_cols_pair = std::max(li.max_cols_pair, lj.max_cols_pair);
+  const int mid_elems = pair ? 2 * li.max_out : 0;  // the outputs of two level-l nodes
+  const int rpt = max_rows <= strm::TCT ? 1 : 2;
   // per-SM shared memory 228 KB: each CTA also reserves 1 KB and < 1 KB of static storage
   const size_t cap = (size_t)(228 / RG::CTAS - 2) * 1024;
   // the column split of short blocks (one output row per thread only) if its buffer fits
   int split = rpt == 1 && split_short ? 1 : 0;
-  strm::Geo geo = strm::geometry<P, RG>(li.max_in, li.max_out, li.max_cols_pair, rpt, split);
+  strm::Geo geo = strm::geometry<P, RG>(max_in, max_out, max_cols_pair, rpt, split, mid_elems);
   if (split && geo.total > cap) {
     split = 0;
-    geo = strm::geometry<P, RG>(li.max_in, li.max_out, li.max_cols_pair, rpt, split);
+    geo = strm::geometry<P, RG>(max_in, max_out, max_cols_pair, rpt, split, mid_elems);
   }
   if (geo.total > cap) return IDBF_EUNSUPPORTED;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned ctas = (unsigned)std::min<int64_t>(p->m, (int64_t)RG::CTAS * sms);
+  const int64_t units = pair ? p->m / 2 : p->m;
+  const unsigned ctas = (unsigned)std::min<int64_t>(units, (int64_t)RG::CTAS * sms);
   const int x_ok = ((uintptr_t)x % 16 == 0) && ((p->n0 * (int)sizeof(V)) % 16 == 0);
   const int use_bulk = bulk && (l > 0 || x_ok);
   const DevLevel d = p->level(l);
+  const DevLevel d1 = p->level(pair ? l + 1 : l);
   const typename P::mat_t* mat = (const typename P::mat_t*)p->lmat[fmt_of<P>()][l];
+  const typename P::mat_t* mat1 = (const typename P::mat_t*)p->lmat[fmt_of<P>()][pair ? l + 1 : l];
   auto go = [&](auto kern) -> idbf_status {
     IDBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.total));
-    kern<<<ctas, RG::NTHREADS, geo.total, st>>>(d, mat, io, li.max_in, li.max_out, li.max_cols_pair, use_bulk,
-                                                p->d_status, p->wait_limit_ns, p->producer_enabled);
+    kern<<<ctas, RG::NTHREADS, geo.total, st>>>(d, mat, d1, mat1, io, max_in, max_out, max_cols_pair, mid_elems,
+                                                use_bulk, p->d_status, p->wait_limit_ns, p->producer_enabled);
     return IDBF_OK;
   };
-  idbf_status s = rpt == 2 ? go(k_level_stream<P, RG, 2, false>)
-                  : split  ? go(k_level_stream<P, RG, 1, true>)
-                           : go(k_level_stream<P, RG, 1, false>);
+  idbf_status s;
+  if (pair) {
+    s = rpt == 2 ? go(k_level_stream<P, RG, 2, false, true>)
+        : split  ? go(k_level_stream<P, RG, 1, true, true>)
+                 : go(k_level_stream<P, RG, 1, false, true>);
+  } else {
+    s = rpt == 2 ? go(k_level_stream<P, RG, 2, false, false>)
+        : split  ? go(k_level_stream<P, RG, 1, true, false>)
+                 : go(k_level_stream<P, RG, 1, false, false>);
+  }
   if (s != IDBF_OK) return s;
   IDBF_CUDA_TRY(cudaGetLastError());
   return IDBF_OK;
@@ -771,15 +855,23 @@ static idbf_status launch_fwd_variant(Plan* p, int l, int v, const void* x, void
   if (v != 0 && p->uneven) return IDBF_EUNSUPPORTED;  // uneven leaves: the per-node kernel only
   if (v == 7) return launch_warp_node<P>(p, l, io, st, fmt);
   if (v != 0 && fmt == IDBF_STORE_C128) return IDBF_EUNSUPPORTED;  // FP64: per-node or warp-per-node kernel
-  if (v == 14 || v == 15) return launch_stream<P, strm::RingD>(p, l, v == 14, true, x, io, st);
+  if (v >= kFirstPairVariant) {  // levels l and l + 1 fused (win: boundary l - 1, wout: boundary l + 1)
+    switch (v - kFirstPairVariant) {
+      case 0: return launch_stream<P, strm::RingA>(p, l, true, true, true, x, io, st);
+      case 1: return launch_stream<P, strm::RingB>(p, l, true, true, true, x, io, st);
+      case 2: return launch_stream<P, strm::RingC>(p, l, true, true, true, x, io, st);
+      default: return launch_stream<P, strm::RingD>(p, l, true, true, true, x, io, st);
+    }
+  }
+  if (v == 14 || v == 15) return launch_stream<P, strm::RingD>(p, l, false, v == 14, true, x, io, st);
   const bool split = v >= 8;
   switch (split ? v - 7 : v) {
-    case 1: return launch_stream<P, strm::RingA>(p, l, true, split, x, io, st);
-    case 2: return launch_stream<P, strm::RingA>(p, l, false, split, x, io, st);
-    case 3: return launch_stream<P, strm::RingB>(p, l, true, split, x, io, st);
-    case 4: return launch_stream<P, strm::RingB>(p, l, false, split, x, io, st);
-    case 5: return launch_stream<P, strm::RingC>(p, l, true, split, x, io, st);
-    case 6: return launch_stream<P, strm::RingC>(p, l, false, split, x, io, st);
+    case 1: return launch_stream<P, strm::RingA>(p, l, false, true, split, x, io, st);
+    case 2: return launch_stream<P, strm::RingA>(p, l, false, false, split, x, io, st);
+    case 3: return launch_stream<P, strm::RingB>(p, l, false, true, split, x, io, st);
+    case 4: return launch_stream<P, strm::RingB>(p, l, false, false, split, x, io, st);
+    case 5: return launch_stream<P, strm::RingC>(p, l, false, true, split, x, io, st);
+    case 6: return launch_stream<P, strm::RingC>(p, l, false, false, split, x, io, st);
     default: break;
   }
   const LevelInfo& li = p->lv[l];
@@ -812,10 +904,49 @@ idbf_status ensure_workspace(Plan* p, int64_t nrhs) {
   return IDBF_OK;
 }
 
+// Forward apply of one right-hand side: per level the autotuned variant (else the default). A
+// pair variant on level l runs levels l and l + 1 in one launch. Each launch reads the buffer the
+// previous one wrote and writes the other one.
+template <class P>
+static idbf_status run_fwd1(Plan* p, const void* x, void* y, int64_t ld, cudaStream_t st, int fmt) {
+  using V = typename P::vec_t;
+  V* wb[2] = {(V*)p->d_ws, (V*)((char*)p->d_ws + (size_t)p->max_seg_total * 16)};
+  int cur = 1;  // buffer holding the last boundary written (boundary b in b % 2 without pairs)
+  for (int l = 0; l <= p->L;) {
+    int v = p->uneven ? 0
+            : p->tuned[fmt].size() > (size_t)l && p->tuned[fmt][l] >= 0 ? p->tuned[fmt][l] : default_variant(fmt);
+    const bool pair = is_pair_variant(v) && l < p->L;
+    const int last = pair ? l + 1 : l;  // level whose outputs this launch writes
+    const V* win = l > 0 ? wb[cur] : nullptr;
+    V* wout = last < p->L ? wb[cur ^ 1] : nullptr;
+    (void)ld;
+    idbf_status s = IDBF_EUNSUPPORTED;
+    if (is_pair_variant(v) && !pair) v = default_variant(fmt);  // a pair variant on level L: one level
+    s = launch_fwd_variant<P>(p, l, v, x, y, win, wout, st, fmt);
+    if (s == IDBF_EUNSUPPORTED && pair) {  // the pair does not fit: level l alone, into the next buffer
+      V* wout1 = wb[cur ^ 1];               // l < L here, so level l writes a workspace boundary
+      s = launch_fwd_variant<P>(p, l, default_variant(fmt), x, y, win, wout1, st, fmt);
+      if (s == IDBF_EUNSUPPORTED) s = launch_fwd_variant<P>(p, l, 0, x, y, win, wout1, st, fmt);
+      if (s != IDBF_OK) return s;
+      if (l < p->L) cur ^= 1;
+      ++l;
+      continue;
+    }
+    if (s == IDBF_EUNSUPPORTED && v != 0) s = launch_fwd_variant<P>(p, l, 0, x, y, win, wout, st, fmt);
+    if (s != IDBF_OK) return s;
+    if (last < p->L) cur ^= 1;
+    l = last + 1;
+  }
+  return IDBF_OK;
+}
+
 template <class P, int RB>
 static idbf_status run_levels(Plan* p, const void* x, void* y, int64_t R, int64_t ld, bool adjoint, cudaStream_t st,
                               int fmt) {
   using V = typename P::vec_t;
+  if constexpr (RB == 1) {
+    if (!adjoint && R == 1) return run_fwd1<P>(p, x, y, ld, st, fmt);
+  }
   V* ws0 = (V*)p->d_ws;
   V* ws1 = (V*)((char*)p->d_ws + (size_t)p->max_seg_total * R * 16);
   const int nlev = p->L + 1;
@@ -1081,35 +1212,67 @@ static idbf_status autotune_fmt(Plan* p, int fmt, cudaStream_t st, int reps, flo
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // workspace filled with real values: every level once, boundary b left in buffer b % 2
   p->tuned[fmt].assign(p->L + 1, -1);
-  s = run_levels<P, 1>(p, x, y, 1, p->N, false, st, fmt);  // fills the workspace with real values
-  float total = 0.f;
-  for (int l = 0; l <= p->L && s == IDBF_OK; ++l) {
+  s = run_levels<P, 1>(p, x, y, 1, p->N, false, st, fmt);
+  // best time of one variant (single level: v < kFirstPairVariant; else the pair l, l + 1)
+  auto time_variant = [&](int l, int v, float* ms_out) -> idbf_status {
     const V* win = l > 0 ? wb[(l - 1) & 1] : nullptr;
-    V* wout = l < p->L ? wb[l & 1] : nullptr;
-    float best = 1e30f;
-    int bestv = default_variant(fmt);
-    for (int v = 0; v < kNumFwdVariants; ++v) {
-      idbf_status r = launch_fwd_variant<P>(p, l, v, x, y, win, wout, st, fmt);
+    const int last = is_pair_variant(v) ? l + 1 : l;
+    V* wout = last < p->L ? wb[l & 1] : nullptr;  // a pair's output goes to the other buffer too
+    idbf_status r = launch_fwd_variant<P>(p, l, v, x, y, win, wout, st, fmt);
+    if (r != IDBF_OK) return r;
+    cudaEventRecord(e0, st);
+    for (int k = 0; k < reps; ++k) launch_fwd_variant<P>(p, l, v, x, y, win, wout, st, fmt);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return IDBF_ECUDA;
+    cudaEventElapsedTime(ms_out, e0, e1);
+    return IDBF_OK;
+  };
+  const int nl = p->L + 1;
+  std::vector<float> one(nl, 1e30f), two(nl, 1e30f);
+  std::vector<int> one_v(nl, default_variant(fmt)), two_v(nl, -1);
+  for (int l = 0; l < nl && s == IDBF_OK; ++l) {
+    for (int v = 0; v < kNumFwdVariants && s == IDBF_OK; ++v) {
+      if (is_pair_variant(v) && l == p->L) continue;
+      float ms = 0.f;
+      const idbf_status r = time_variant(l, v, &ms);
       if (r == IDBF_EUNSUPPORTED) continue;
       if (r != IDBF_OK) { s = r; break; }
-      cudaEventRecord(e0, st);
-      for (int k = 0; k < reps; ++k) launch_fwd_variant<P>(p, l, v, x, y, win, wout, st, fmt);
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) { s = IDBF_ECUDA; break; }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; bestv = v; }
+      if (is_pair_variant(v)) {
+        if (ms < two[l]) { two[l] = ms; two_v[l] = v; }
+      } else if (ms < one[l]) {
+        one[l] = ms; one_v[l] = v;
+      }
     }
-    p->tuned[fmt][l] = bestv;
-    total += best / reps;
+  }
+  // the cheapest way to cover levels 0..L with single levels and fused pairs (left to right, as
+  // run_fwd1 reads the choices)
+  std::vector<float> cost(nl + 1, 0.f);
+  std::vector<int> take_pair(nl, 0);
+  for (int l = nl - 1; l >= 0; --l) {
+    cost[l] = one[l] + cost[l + 1];
+    if (l + 1 < nl && two_v[l] >= 0 && two[l] + cost[l + 2] < cost[l]) {
+      cost[l] = two[l] + cost[l + 2];
+      take_pair[l] = 1;
+    }
+  }
+  p->tuned[fmt].assign(nl, -1);
+  for (int l = 0; l < nl;) {
+    if (take_pair[l]) {
+      p->tuned[fmt][l] = p->tuned[fmt][l + 1] = two_v[l];
+      l += 2;
+    } else {
+      p->tuned[fmt][l] = one_v[l];
+      l += 1;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamSynchronize(st);
   cudaFree(x);
   cudaFree(y);
-  if (best_ms_out) *best_ms_out = total;
+  if (best_ms_out) *best_ms_out = cost[0] / reps;
   return s;
 }
 

@@ -168,11 +168,16 @@ def test_every_forward_variant_matches_oracle(case, mode, fmt, tol):
     dt = torch.complex64 if mode == P.MODE_FP32 else torch.complex128
     xd = torch.from_numpy(X).to(dt).cuda()
     ref = idbf.apply(c["F"], X)
+    L = c["F"].L
     for v in range(P.NUM_FWD_VARIANTS):   # FP64 runs variants 0 and 7; the streaming ones fall back to 0
-        plan.set_level_variants(mode, [v] * (c["F"].L + 1))
-        y = plan.apply(xd, mode=mode)
-        plan.sync_status()
-        assert rel(y.cpu().numpy(), ref) < tol, f"variant {v}"
+        # variants 16-19 fuse levels l and l + 1: pairs (0, 1), (2, 3), ... and, shifted by one
+        # level, (1, 2), (3, 4), ..., so that every pair of consecutive levels is fused once
+        patterns = [[v] * (L + 1)] + ([[1] + [v] * L] if v >= 16 else [])
+        for pat in patterns:
+            plan.set_level_variants(mode, pat)
+            y = plan.apply(xd, mode=mode)
+            plan.sync_status()
+            assert rel(y.cpu().numpy(), ref) < tol, f"variant {v}, pattern {pat}"
     ms = plan.autotune(mode, reps=2)
     assert ms > 0
     chosen = plan.stats()["level_variant"][fmt]

@@ -70,9 +70,10 @@ def test_every_variant_and_the_batch_on_degenerate_blocks(tiny, mode, fmt, dt, t
     ref = idbf.apply(tiny["F"], X)
     xd = torch.from_numpy(X.astype(dt)).cuda()
     for v in range(P.NUM_FWD_VARIANTS):
-        plan.set_level_variants(mode, [v] * 3)
-        assert rel(plan.apply(xd, mode=mode).cpu().numpy(), ref) < tol, f"variant {v}"
-        plan.sync_status()
+        for pat in [[v] * 3] + ([[1, v, v]] if v >= 16 else []):  # fused pairs (0, 1) and (1, 2)
+            plan.set_level_variants(mode, pat)
+            assert rel(plan.apply(xd, mode=mode).cpu().numpy(), ref) < tol, f"variant {v}, pattern {pat}"
+            plan.sync_status()
     plan.set_level_variants(mode, [])
     Xb = inputs.complex_gaussian(N, 5, seed=8)
     b = P.Batch([plan, plan], [1, 5], mode=mode)

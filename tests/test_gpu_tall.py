@@ -46,9 +46,10 @@ def test_every_forward_variant_on_tall_blocks(tall, mode, fmt, tol):
     dt = torch.complex64 if mode == P.MODE_FP32 else torch.complex128
     xd = torch.from_numpy(X).to(dt).cuda()
     for v in range(P.NUM_FWD_VARIANTS):
-        plan.set_level_variants(mode, [v] * 3)
-        assert rel(plan.apply(xd, mode=mode).cpu().numpy(), ref) < tol, f"variant {v}"
-        plan.sync_status()
+        for pat in [[v] * 3] + ([[1, v, v]] if v >= 16 else []):  # fused pairs (0, 1) and (1, 2)
+            plan.set_level_variants(mode, pat)
+            assert rel(plan.apply(xd, mode=mode).cpu().numpy(), ref) < tol, f"variant {v}, pattern {pat}"
+            plan.sync_status()
     plan.autotune(mode, reps=2)
     assert rel(plan.apply(xd, mode=mode).cpu().numpy(), ref) < tol
 
