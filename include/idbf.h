@@ -84,6 +84,13 @@ typedef struct {
 #define IDBF_SAMPLE_RANDOM 1         /* uniform without replacement, SplitMix64 stream per ID */
 #define IDBF_SAMPLE_ALL 2            /* no sampling (every candidate); exact-mode checks */
 
+/* arithmetic of the IDs' column-pivoted Householder QR and back substitution (Sec. 2.1):
+ * FP64 (default), or double-float (binary32 pairs, 48 significant bits) for the O(ns b k) updates
+ * with the O(b)-per-step scalars in FP64, which runs on the FP32 pipes (the build is bound by
+ * the FP64 pipe otherwise); both far more accurate than any tolerance eps >= 1e-12 needs */
+#define IDBF_QR_FP64 0
+#define IDBF_QR_DF64 1
+
 /* storage formats of the factor entries on the device (bit i of a storage mask = format i) */
 #define IDBF_STORE_C128 0 /* complex FP64, 16 B per entry */
 #define IDBF_STORE_DF64 1 /* complex double-float: (re_hi, re_lo, im_hi, im_lo) floats, 16 B */
@@ -98,10 +105,12 @@ typedef struct {
   int32_t sampling;       /* IDBF_SAMPLE_* */
   int32_t storage;        /* IDBF_STORE_* format the factors are kept in after the build */
   uint64_t seed;          /* random sampling stream seed */
+  int32_t qr_arith;       /* IDBF_QR_* arithmetic of the pivoted QR of every ID */
+  int32_t reserved;       /* 0 */
 } idbf_params;
 
 /* Fill p with the defaults: eps 1e-6, t 1, t_leaf = t, n0 64, k = min dims, Mock-Chebyshev,
- * C128 storage, seed 0. */
+ * C128 storage, seed 0, FP64 QR. */
 void idbf_default_params(idbf_params* p);
 
 /* idbf_build - construct the IDBF of K on the point sets X = {x_i} and Omega = {xi_j}

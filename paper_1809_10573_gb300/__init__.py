@@ -14,12 +14,12 @@ import torch
 
 from . import _lib
 from ._lib import (KERNEL_DFT, KERNEL_FIO1D, KERNEL_J0, MODE_DF64, MODE_FP32, MODE_FP64, MODE_TF32X3,
-                   MODE_TF32X3_S64, NUM_FWD_VARIANTS, SAMPLE_ALL, SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, STORE_C64, STORE_C128,
+                   MODE_TF32X3_S64, NUM_FWD_VARIANTS, QR_DF64, QR_FP64, SAMPLE_ALL, SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, STORE_C64, STORE_C128,
                    STORE_DF64, IDBFError)
 
 __all__ = ["Plan", "Batch", "IDBFError", "apply", "IDBFApply", "kernel_matvec_rows", "dyadic_leaves", "tree_depth", "KERNEL_FIO1D", "KERNEL_DFT", "KERNEL_J0", "MODE_FP64",
            "MODE_DF64", "MODE_FP32", "MODE_TF32X3", "MODE_TF32X3_S64", "STORE_C128", "STORE_DF64", "STORE_C64",
-           "SAMPLE_MOCK_CHEBYSHEV", "SAMPLE_RANDOM", "SAMPLE_ALL", "NUM_FWD_VARIANTS"]
+           "SAMPLE_MOCK_CHEBYSHEV", "SAMPLE_RANDOM", "SAMPLE_ALL", "NUM_FWD_VARIANTS", "QR_FP64", "QR_DF64"]
 
 _VEC_DTYPE = {MODE_FP64: torch.complex128, MODE_DF64: torch.complex128,
               MODE_FP32: torch.complex64, MODE_TF32X3: torch.complex64, MODE_TF32X3_S64: torch.complex64}
@@ -56,13 +56,13 @@ class Plan:
     @classmethod
     def build(cls, x, xi, eps=1e-6, leaf=64, kernel="fio", c_profile=0, sign=-1, rank_cap=0,
               oversample=1.0, oversample_leaf=0.0, sampling=SAMPLE_MOCK_CHEBYSHEV, seed=0,
-              storage=STORE_C128, stream=None):
+              storage=STORE_C128, qr_arith=QR_FP64, stream=None):
         L = _lib.lib()
         k = _lib.Kernel(_kernel_kind(kernel), sign, c_profile, 0)
         p = _lib.Params()
         L.idbf_default_params(C.byref(p))
         p.eps, p.leaf, p.rank_cap, p.oversample, p.oversample_leaf = eps, leaf, rank_cap, oversample, oversample_leaf
-        p.sampling, p.seed, p.storage = sampling, seed, storage
+        p.sampling, p.seed, p.storage, p.qr_arith = sampling, seed, storage, qr_arith
         xa = np.ascontiguousarray(x, dtype=np.float64)
         xia = np.ascontiguousarray(xi, dtype=np.float64)
         out = C.c_void_p()
@@ -76,14 +76,14 @@ class Plan:
     @classmethod
     def build_leaves(cls, x, xi, L, row_leaf_off, col_leaf_off, eps=1e-6, kernel="dft", c_profile=0, sign=-1,
                      rank_cap=0, oversample=1.0, oversample_leaf=0.0, sampling=SAMPLE_MOCK_CHEBYSHEV, seed=0,
-                     storage=STORE_C128, stream=None):
+                     storage=STORE_C128, qr_arith=QR_FP64, stream=None):
         """idbf_build_leaves: the construction on trees whose 2^L leaves are given by offsets."""
         L_ = _lib.lib()
         k = _lib.Kernel(_kernel_kind(kernel), sign, c_profile, 0)
         p = _lib.Params()
         L_.idbf_default_params(C.byref(p))
         p.eps, p.rank_cap, p.oversample, p.oversample_leaf = eps, rank_cap, oversample, oversample_leaf
-        p.sampling, p.seed, p.storage = sampling, seed, storage
+        p.sampling, p.seed, p.storage, p.qr_arith = sampling, seed, storage, qr_arith
         xa = np.ascontiguousarray(x, dtype=np.float64)
         xia = np.ascontiguousarray(xi, dtype=np.float64)
         ro = np.ascontiguousarray(row_leaf_off, dtype=np.int64)

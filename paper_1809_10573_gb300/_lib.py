@@ -15,6 +15,7 @@ OK, EINVAL, ENOMEM, ECUDA, ERANKCAP, ETIMEOUT, EFORMAT, EUNSUPPORTED = range(8)
 KERNEL_FIO1D, KERNEL_DFT, KERNEL_J0 = 0, 1, 2
 SAMPLE_MOCK_CHEBYSHEV, SAMPLE_RANDOM, SAMPLE_ALL = 0, 1, 2
 STORE_C128, STORE_DF64, STORE_C64 = 0, 1, 2
+QR_FP64, QR_DF64 = 0, 1
 MODE_FP64, MODE_DF64, MODE_FP32, MODE_TF32X3, MODE_TF32X3_S64 = 0, 1, 2, 3, 4
 NUM_FWD_VARIANTS = 20  # IDBF_NUM_FWD_VARIANTS
 MAX_LEVELS = 48
@@ -28,7 +29,7 @@ class Kernel(C.Structure):
 class Params(C.Structure):
     _fields_ = [("eps", C.c_double), ("oversample", C.c_double), ("oversample_leaf", C.c_double),
                 ("leaf", C.c_int32), ("rank_cap", C.c_int32), ("sampling", C.c_int32),
-                ("storage", C.c_int32), ("seed", C.c_uint64)]
+                ("storage", C.c_int32), ("seed", C.c_uint64), ("qr_arith", C.c_int32), ("reserved", C.c_int32)]
 
 
 class HostFactors(C.Structure):

@@ -202,6 +202,17 @@ __global__ void k_sample(const IDDesc* __restrict__ D, int64_t nid, const int32_
 // ---- kernel entries of the sampled block ----------------------------------------------------
 // row ID (side 0): QR matrix A(i, c) = K(x[b_c], xi[s_i]) (the transpose of the sampled block)
 // column ID (side 1): A(i, c) = K(x[s_i], xi[b_c])
+// Entries are FP64 (double2) or, for the double-float QR, split into (re_hi, re_lo, im_hi, im_lo)
+// binary32 parts (float4, the same 16 bytes): hi = fl32(v), lo = fl32(v - hi).
+__device__ __forceinline__ float4 df_split(double2 v) {
+  const float rh = (float)v.x, ih = (float)v.y;
+  return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+__device__ __forceinline__ double2 df_join(float4 v) {
+  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
+template <bool DF>
 __global__ void k_fill(const IDDesc* __restrict__ D, const int32_t* __restrict__ bl, const int32_t* __restrict__ sp,
                        const double* __restrict__ x, const double* __restrict__ cx, const double* __restrict__ xi,
                        double2* __restrict__ A, KDesc K, int side) {
@@ -213,7 +224,9 @@ __global__ void k_fill(const IDDesc* __restrict__ D, const int32_t* __restrict__
     const int32_t bc = b[c];
     for (int i = threadIdx.x; i < d.ns; i += blockDim.x) {
       const int32_t si = s[i];
-      a[(int64_t)c * d.ns + i] = side == 0 ? kentry(K, x[bc], cx[bc], xi[si]) : kentry(K, x[si], cx[si], xi[bc]);
+      const double2 v = side == 0 ? kentry(K, x[bc], cx[bc], xi[si]) : kentry(K, x[si], cx[si], xi[bc]);
+      if constexpr (DF) ((float4*)a)[(int64_t)c * d.ns + i] = df_split(v);
+      else a[(int64_t)c * d.ns + i] = v;
     }
   }
 }
@@ -407,6 +420,244 @@ __global__ void __launch_bounds__(NT) k_qr(const IDDesc* __restrict__ D, double2
   }
 }
 
+// ---- the same QR in double-float arithmetic ---------------------------------------------------
+// GB300 runs FP32 at ~63x its FP64 rate (cuBLAS: 69.7 against 1.10 TFLOP/s), and the Householder
+// updates above keep its FP64 pipe ~93 % busy. Here every O(ns b) loop runs in double-float:
+// each complex entry is (re_hi, re_lo, im_hi, im_lo) binary32 parts (48 significant bits, Dekker
+// 1971), products are formed exactly with FMA and sums with Knuth's TwoSum (Ogita, Rump and Oishi
+// 2005; Joldes, Muller and Popescu 2017). The per-step and per-column scalars (norm, reflector
+// coefficients, the back-substitution quotients) are computed in FP64 from the double-float
+// values, O(b) and O(k b) operations per ID, not O(ns b k). Pivoting compares FP32 column norms;
+// the rank test uses the double-float norm of the pivot column. The result (R and T in A) has
+// double-float accuracy, far below any ID tolerance eps >= 1e-12.
+__device__ __forceinline__ void df2_sum(float a, float b, float& s, float& e) {  // TwoSum (Knuth)
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void df2_fast(float a, float b, float& s, float& e) {  // Fast2Sum, |a| >= |b|
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// (s, c) accumulates a * b for double-float a = (ah, al), b = (bh, bl): the high product exactly
+// (p + e), the cross terms into the compensation, p into s by TwoSum
+__device__ __forceinline__ void df2_dot(float& s, float& c, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  float t, err;
+  df2_sum(s, p, t, err);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+// (h, l) += (s, c), renormalised
+__device__ __forceinline__ void df2_acc(float& h, float& l, float s, float c) {
+  float t, e;
+  df2_sum(h, s, t, e);
+  e = __fadd_rn(e, __fadd_rn(l, c));
+  df2_fast(t, e, h, l);
+}
+__device__ __forceinline__ float4 df_neg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+// z - f w for double-float complex z, f, w (real parts .x/.y, imaginary .z/.w)
+__device__ __forceinline__ float4 df_cmsub(float4 z, float4 f, float4 w) {
+  float sr = z.x, cr = z.y, si = z.z, ci = z.w;
+  df2_dot(sr, cr, -f.x, -f.y, w.x, w.y);
+  df2_dot(sr, cr, f.z, f.w, w.z, w.w);
+  df2_dot(si, ci, -f.x, -f.y, w.z, w.w);
+  df2_dot(si, ci, -f.z, -f.w, w.x, w.y);
+  float4 r;
+  df2_fast(sr, cr, r.x, r.y);
+  df2_fast(si, ci, r.z, r.w);
+  return r;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum_d(double v, double* rv) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) rv[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < NT / 32 ? rv[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) rv[0] = v;
+  }
+  __syncthreads();
+  v = rv[0];
+  __syncthreads();
+  return v;
+}
+
+// As k_qr, on double-float entries (float4); same outputs: kout, perm in pscr, T in A(0:k, k:b).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_qr_df(const IDDesc* __restrict__ D, double2* __restrict__ Araw,
+                                              int32_t* __restrict__ pscr, int32_t* __restrict__ kout,
+                                              int32_t* __restrict__ satur, double eps) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const IDDesc d = D[blockIdx.x];
+  const int ns = d.ns, b = d.b, kmax = d.kmax;
+  float4* A = (float4*)(Araw + d.a_off);
+  float4* v = (float4*)smraw;                 // Householder vector, ns (double-float complex)
+  float* nrm = (float*)(v + ns);              // FP32 squared column norms (pivot choice), b
+  int* perm = (int*)(nrm + b);                // b
+  __shared__ double rv[NT / 32];
+  __shared__ float rvf[NT / 32];
+  __shared__ int ri[NT / 32];
+  __shared__ float4 sh_beta;
+  __shared__ double sh_coef;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NT / 32;
+  for (int c = tid; c < b; c += NT) perm[c] = c;
+  for (int c = warp; c < b; c += NW) {
+    const float4* col = A + (int64_t)c * ns;
+    float s = 0.f;
+    for (int i = lane; i < ns; i += 32) { const float4 z = col[i]; s = fmaf(z.x, z.x, fmaf(z.z, z.z, s)); }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) nrm[c] = s;
+  }
+  __syncthreads();
+  double r11 = 0.0;
+  int k = 0;
+  bool zero_block = false;
+  for (int j = 0; j < kmax; ++j) {
+    // pivot: the largest FP32 column norm (ties to the lowest index)
+    float best = -1.f;
+    int bi = 0x7fffffff;
+    for (int c = j + tid; c < b; c += NT)
+      if (nrm[c] > best) { best = nrm[c]; bi = c; }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { rvf[warp] = best; ri[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < NW ? rvf[lane] : -1.f;
+      bi = lane < NW ? ri[lane] : 0x7fffffff;
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) ri[0] = bi;
+    }
+    __syncthreads();
+    bi = ri[0];
+    __syncthreads();
+    // move the pivot column to position j
+    if (bi != j) {
+      float4* cj = A + (int64_t)j * ns;
+      float4* cp = A + (int64_t)bi * ns;
+      for (int i = tid; i < ns; i += NT) { const float4 t = cj[i]; cj[i] = cp[i]; cp[i] = t; }
+      __syncthreads();
+      if (tid == 0) {
+        const float tn = nrm[j]; nrm[j] = nrm[bi]; nrm[bi] = tn;
+        const int tp = perm[j]; perm[j] = perm[bi]; perm[bi] = tp;
+      }
+    }
+    __syncthreads();
+    // the pivot column's norm in double-float, then the rank test (Eq. acc) in FP64
+    float4* cj = A + (int64_t)j * ns;
+    double a2;
+    {
+      float sh = 0.f, sc = 0.f;
+      for (int i = j + tid; i < ns; i += NT) {
+        const float4 z = cj[i];
+        df2_dot(sh, sc, z.x, z.y, z.x, z.y);
+        df2_dot(sh, sc, z.z, z.w, z.z, z.w);
+      }
+      a2 = block_sum_d<NT>((double)sh + (double)sc, rv);
+    }
+    const double rjj = sqrt(a2);
+    if (j == 0) {
+      r11 = rjj;
+      if (!(r11 > 0.0)) { zero_block = true; break; }
+    } else if (rjj <= eps * r11) {
+      break;
+    }
+    // Householder reflector H = I - 2 v v^* / (v^* v) with H x = beta e_1, x = A(j:ns, j)
+    if (tid == 0) {
+      const double alpha = rjj;
+      const double2 x0 = df_join(cj[j]);
+      const double ax0 = hypot(x0.x, x0.y);
+      const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+      const double2 beta = make_double2(-ph.x * alpha, -ph.y * alpha);
+      sh_beta = df_split(beta);
+      v[0] = df_split(make_double2(x0.x - beta.x, x0.y - beta.y));
+      sh_coef = 2.0 / (2.0 * a2 + 2.0 * alpha * ax0);  // 2 / (v^* v)
+    }
+    for (int i = j + 1 + tid; i < ns; i += NT) v[i - j] = cj[i];
+    __syncthreads();
+    const double coef = sh_coef;
+    // trailing columns: a -= coef v (v^* a); FP32 norms of rows j+1.. recomputed
+    for (int c = j + 1 + warp; c < b; c += NW) {
+      float4* col = A + (int64_t)c * ns;
+      float dr = 0.f, er = 0.f, di = 0.f, ei = 0.f;  // v^* a: (sum, compensation) per part
+      for (int i = j + lane; i < ns; i += 32) {
+        const float4 z = col[i], w = v[i - j];
+        df2_dot(dr, er, w.x, w.y, z.x, z.y);   // Re: wr zr + wi zi
+        df2_dot(dr, er, w.z, w.w, z.z, z.w);
+        df2_dot(di, ei, w.x, w.y, z.z, z.w);   // Im: wr zi - wi zr
+        df2_dot(di, ei, -w.z, -w.w, z.x, z.y);
+      }
+      float hr, lr, hi, li;
+      df2_fast(dr, er, hr, lr);
+      df2_fast(di, ei, hi, li);
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ohr = __shfl_xor_sync(0xffffffffu, hr, o), olr = __shfl_xor_sync(0xffffffffu, lr, o);
+        const float ohi = __shfl_xor_sync(0xffffffffu, hi, o), oli = __shfl_xor_sync(0xffffffffu, li, o);
+        df2_acc(hr, lr, ohr, olr);
+        df2_acc(hi, li, ohi, oli);
+      }
+      const double2 f = make_double2(coef * ((double)hr + (double)lr), coef * ((double)hi + (double)li));
+      const float4 fd = df_split(f);
+      float s = 0.f;
+      for (int i = j + lane; i < ns; i += 32) {
+        const float4 z = df_cmsub(col[i], fd, v[i - j]);
+        col[i] = z;
+        if (i > j) s = fmaf(z.x, z.x, fmaf(z.z, z.z, s));
+      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) nrm[c] = s;
+    }
+    if (tid == 0) cj[j] = sh_beta;
+    __syncthreads();
+    k = j + 1;
+  }
+  int32_t* pout = pscr + d.bl_off;  // same offsets as the b list
+  for (int c = tid; c < b; c += NT) pout[c] = perm[c];
+  if (zero_block) {
+    k = 1;
+    for (int c = 1 + tid; c < b; c += NT) A[(int64_t)c * ns] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (tid == 0) {
+    kout[blockIdx.x] = k;
+    // stopped at the cap, not by eps (an empty block, kmax = 0, has rank 0 by definition)
+    satur[blockIdx.x] = (!zero_block && kmax > 0 && k == kmax && kmax < b) ? 1 : 0;
+  }
+  __syncthreads();
+  if (zero_block) return;
+  // T = R11^{-1} R12 by column-oriented back substitution, a warp per column of R12; the
+  // quotient in FP64, the updates in double-float
+  for (int c = k + warp; c < b; c += NW) {
+    float4* col = A + (int64_t)c * ns;
+    for (int i = k - 1; i >= 0; --i) {
+      __syncwarp();
+      const double2 rii = df_join(A[(int64_t)i * ns + i]);
+      const double2 num = df_join(col[i]);
+      const double den = rii.x * rii.x + rii.y * rii.y;
+      const double2 t = make_double2((num.x * rii.x + num.y * rii.y) / den, (num.y * rii.x - num.x * rii.y) / den);
+      const float4 td = df_split(t);
+      const float4* ci = A + (int64_t)i * ns;
+      for (int l = lane; l < i; l += 32) col[l] = df_cmsub(col[l], ci[l], td);
+      __syncwarp();
+      if (lane == 0) col[i] = td;
+    }
+  }
+}
+
 // ---- emit: sorted skeleton, index lists and the interpolation block -------------------------
 struct EmitDesc {
   int64_t t_off;    // output block offset (complex entries) in the batch result
@@ -416,6 +667,7 @@ struct EmitDesc {
 
 // side 0 (row ID): block M = T^T (n_p x k), column-major: M(c, r') at r' n_p + c
 // side 1 (column ID): block M = T (k x n_p), column-major: M(r', c) at c k + r'
+template <bool DF>
 __global__ void k_emit(const IDDesc* __restrict__ D, const EmitDesc* __restrict__ E, const double2* __restrict__ Aall,
                        const int32_t* __restrict__ pscr, const int32_t* __restrict__ bl, const int32_t* __restrict__ kin,
                        double2* __restrict__ Tout, int32_t* __restrict__ Iout, int32_t* __restrict__ Sout, int side) {
@@ -441,13 +693,14 @@ __global__ void k_emit(const IDDesc* __restrict__ D, const EmitDesc* __restrict_
   }
   for (int c = threadIdx.x; c < np; c += blockDim.x) Iout[e.i_off + k + c] = perm[k + c];
   const double2* A = Aall + d.a_off;
+  auto at = [&](int64_t i) -> double2 { return DF ? df_join(((const float4*)A)[i]) : A[i]; };
   for (int64_t t = threadIdx.x; t < (int64_t)k * np; t += blockDim.x) {
     if (side == 0) {
       const int r = (int)(t / np), c = (int)(t % np);
-      Tout[e.t_off + t] = A[(int64_t)(k + c) * ns + order[r]];
+      Tout[e.t_off + t] = at((int64_t)(k + c) * ns + order[r]);
     } else {
       const int c = (int)(t / k), r = (int)(t % k);
-      Tout[e.t_off + t] = A[(int64_t)(k + c) * ns + order[r]];
+      Tout[e.t_off + t] = at((int64_t)(k + c) * ns + order[r]);
     }
   }
 }
@@ -713,13 +966,21 @@ idbf_status Builder::run_step(int side, int s) {
                                                                     prm.sampling, cap, maxns);
     TRY_CUDA(cudaGetLastError());
     dim3 gf((unsigned)nb, (unsigned)std::min(maxb, 64));
-    k_fill<<<gf, 256, 0, st>>>(dD, (int32_t*)blist.p, (int32_t*)samp.p, d_x, d_cx, d_xi, (double2*)A.p, K, side);
+    const bool df = prm.qr_arith == IDBF_QR_DF64;
+    if (df) k_fill<true><<<gf, 256, 0, st>>>(dD, (int32_t*)blist.p, (int32_t*)samp.p, d_x, d_cx, d_xi, (double2*)A.p, K, side);
+    else k_fill<false><<<gf, 256, 0, st>>>(dD, (int32_t*)blist.p, (int32_t*)samp.p, d_x, d_cx, d_xi, (double2*)A.p, K, side);
     TRY_CUDA(cudaGetLastError());
     const size_t smQ = (size_t)maxns * 16 + (size_t)maxb * 12 + 16;
     if (smQ > 200 * 1024) { free_res(); return IDBF_EUNSUPPORTED; }
-    TRY_CUDA(cudaFuncSetAttribute(k_qr<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smQ));
-    k_qr<256><<<(unsigned)nb, 256, smQ, st>>>(dD, (double2*)A.p, (int32_t*)pscr.p, (int32_t*)kbuf.p, (int32_t*)satbuf.p,
-                                             prm.eps);
+    if (df) {
+      TRY_CUDA(cudaFuncSetAttribute(k_qr_df<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smQ));
+      k_qr_df<256><<<(unsigned)nb, 256, smQ, st>>>(dD, (double2*)A.p, (int32_t*)pscr.p, (int32_t*)kbuf.p,
+                                                  (int32_t*)satbuf.p, prm.eps);
+    } else {
+      TRY_CUDA(cudaFuncSetAttribute(k_qr<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smQ));
+      k_qr<256><<<(unsigned)nb, 256, smQ, st>>>(dD, (double2*)A.p, (int32_t*)pscr.p, (int32_t*)kbuf.p,
+                                               (int32_t*)satbuf.p, prm.eps);
+    }
     TRY_CUDA(cudaGetLastError());
     std::vector<int32_t> kb(nb), sb(nb);
     TRY_CUDA(cudaMemcpyAsync(kb.data(), kbuf.p, nb * 4, cudaMemcpyDeviceToHost, st));
@@ -748,9 +1009,10 @@ idbf_status Builder::run_step(int side, int s) {
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) { free_res(); cudaGetLastError(); return IDBF_ENOMEM; }
     if ((e = emits.ensure(nb * sizeof(EmitDesc))) != cudaSuccess) { free_res(); return IDBF_ENOMEM; }
     TRY_CUDA(cudaMemcpyAsync(emits.p, E.data(), nb * sizeof(EmitDesc), cudaMemcpyHostToDevice, st));
-    k_emit<<<(unsigned)nb, 256, (size_t)maxk * 8, st>>>(dD, (EmitDesc*)emits.p, (double2*)A.p, (int32_t*)pscr.p,
-                                                      (int32_t*)blist.p, (int32_t*)kbuf.p, (double2*)res.back().T,
-                                                      res.back().I, res.back().S, side);
+    auto emit = df ? k_emit<true> : k_emit<false>;
+    emit<<<(unsigned)nb, 256, (size_t)maxk * 8, st>>>(dD, (EmitDesc*)emits.p, (double2*)A.p, (int32_t*)pscr.p,
+                                                    (int32_t*)blist.p, (int32_t*)kbuf.p, (double2*)res.back().T,
+                                                    res.back().I, res.back().S, side);
     TRY_CUDA(cudaGetLastError());
     TRY_CUDA(cudaStreamSynchronize(st));
   }
@@ -976,7 +1238,7 @@ static idbf_status build_plan(const idbf_kernel* kernel, const double* x_host, c
     }
   }
   if (!(pr.eps >= 0.0) || !(pr.oversample >= 1.0) || pr.rank_cap < 0 || pr.sampling < 0 || pr.sampling > 2 ||
-      pr.storage < 0 || pr.storage > 2)
+      pr.storage < 0 || pr.storage > 2 || (pr.qr_arith != IDBF_QR_FP64 && pr.qr_arith != IDBF_QR_DF64))
     return IDBF_EINVAL;
   if (kernel->kind == IDBF_KERNEL_FIO1D) {
     if (kernel->c_profile < 0 || kernel->c_profile > 2) return IDBF_EINVAL;

@@ -361,6 +361,8 @@ void idbf_default_params(idbf_params* p) {
   p->sampling = IDBF_SAMPLE_MOCK_CHEBYSHEV;
   p->storage = IDBF_STORE_C128;
   p->seed = 0;
+  p->qr_arith = IDBF_QR_FP64;
+  p->reserved = 0;
 }
 
 const char* idbf_strerror(idbf_status s) {

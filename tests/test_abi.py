@@ -91,7 +91,7 @@ def test_python_constants_match_the_header():
     src = open(HEADER).read()
     defs = dict(re.findall(r"#define (IDBF_[A-Z0-9_]+) (\d+)\b", src))
     pairs = {"IDBF_NUM_FWD_VARIANTS": P.NUM_FWD_VARIANTS, "IDBF_MODE_TF32X3": P.MODE_TF32X3,
-             "IDBF_MODE_TF32X3_S64": P.MODE_TF32X3_S64,
+             "IDBF_MODE_TF32X3_S64": P.MODE_TF32X3_S64, "IDBF_QR_DF64": P.QR_DF64,
              "IDBF_MODE_FP32": P.MODE_FP32, "IDBF_STORE_C64": P.STORE_C64, "IDBF_KERNEL_J0": P.KERNEL_J0,
              "IDBF_SAMPLE_ALL": P.SAMPLE_ALL}
     for name, val in pairs.items():
@@ -144,7 +144,7 @@ def test_ctypes_structures_match_the_c_layout(tmp_path):
         pytest.skip("no C compiler")
     checks = [("idbf_stats_t", _lib.Stats, ["entries", "segment_entries", "device_bytes", "level_variant",
                                             "level_storage"]),
-              ("idbf_params", _lib.Params, ["leaf", "seed"]),
+              ("idbf_params", _lib.Params, ["leaf", "seed", "qr_arith"]),
               ("idbf_host_factors", _lib.HostFactors, ["seg_len", "mat_len", "idx_len", "col_leaf_off"]),
               ("idbf_kernel", _lib.Kernel, ["c_profile"])]
     body = []

@@ -53,10 +53,11 @@ def test_exact_mode_dft():
     (2048, 8, 1e-6, "uniform", "fio", 1, {}),                                            # Example 1
     (4096, 64, 1e-6, "schlomilch", "j0", 0, dict(oversample=2.0, oversample_leaf=4.0)),  # Example 2
 ])
-def test_accuracy_against_dense(N, n0, eps, grid, kind, prof, kw):
+@pytest.mark.parametrize("qr", [P.QR_FP64, P.QR_DF64], ids=["qr_fp64", "qr_df64"])
+def test_accuracy_against_dense(N, n0, eps, grid, kind, prof, kw, qr):
     x, xi = {"uniform": inputs.uniform_grid, "schlomilch": inputs.schlomilch_grid}.get(
         grid, lambda n: inputs.jittered_grid(n, seed=n))(N)
-    plan = P.Plan.build(x, xi, eps=eps, leaf=n0, kernel=kind, c_profile=prof, sign=-1, **kw)
+    plan = P.Plan.build(x, xi, eps=eps, leaf=n0, kernel=kind, c_profile=prof, sign=-1, qr_arith=qr, **kw)
     kinds = {"fio": kernels.KIND_FIO, "dft": kernels.KIND_DFT, "j0": kernels.KIND_J0}
     K = kernels.Kernel(kinds[kind], sign=-1, c_profile=prof)
     g = inputs.complex_gaussian(N, 1, seed=5)[:, 0]
@@ -162,3 +163,33 @@ def test_clone_is_an_independent_bitwise_copy():
     for m, y in want.items():
         got = twin.apply(g if m != P.MODE_FP32 else g.to(torch.complex64), mode=m).cpu()
         assert torch.equal(got, y), m
+
+
+def test_double_float_qr_matches_the_fp64_qr():
+    """The double-float QR of the IDs (the O(ns b k) Householder updates on the FP32 pipes) gives
+    the factorization of the FP64 QR: at N = 2^14 (FIO of the benchmark, eps = 1e-6) the same
+    ranks up to pivot near-ties, and applies that agree within eps of each other; its error
+    against GPU direct rows of K x stays within 10 eps, and the exact mode (no sampling, eps =
+    1e-15) reproduces the DFT to 1e-12."""
+    N = 1 << 14
+    x, xi = inputs.uniform_grid(N)
+    kw = dict(eps=1e-6, leaf=64, kernel="fio", c_profile=0, oversample=2.0, oversample_leaf=4.0)
+    a = P.Plan.build(x, xi, qr_arith=P.QR_FP64, **kw)
+    b = P.Plan.build(x, xi, qr_arith=P.QR_DF64, **kw)
+    sa, sb = a.stats(), b.stats()
+    assert sb["rank_saturated"] == 0
+    assert abs(sa["entries"] - sb["entries"]) <= 2e-3 * sa["entries"]
+    assert all(abs(p - q) <= 2 for p, q in zip(sa["level_kmax"], sb["level_kmax"]))
+    g = torch.from_numpy(inputs.complex_gaussian(N, 1, seed=2)[:, 0]).cuda()
+    ya, yb = a.apply(g), b.apply(g)
+    assert float(torch.linalg.norm(ya - yb) / torch.linalg.norm(ya)) < 1e-6
+    rows = torch.from_numpy(inputs.sample_rows(N, 256, seed=3)).cuda()
+    ud = P.kernel_matvec_rows(torch.from_numpy(x).cuda(), torch.from_numpy(xi).cuda(), g, rows, kernel="fio",
+                              c_profile=0)
+    assert float(torch.linalg.norm(yb[rows] - ud) / torch.linalg.norm(ud)) < 1e-5
+    Ne = 64
+    xe, xie = inputs.uniform_grid(Ne)
+    pe = P.Plan.build(xe, xie, eps=1e-15, leaf=4, kernel="dft", sign=-1, sampling=P.SAMPLE_ALL, qr_arith=P.QR_DF64)
+    ge = inputs.complex_gaussian(Ne, 1, seed=2)[:, 0]
+    ye = pe.apply(torch.from_numpy(ge).cuda()).cpu().numpy()
+    assert rel(ye, (-1.0) ** np.arange(Ne) * np.fft.fft(ge)) < 1e-12

@@ -140,7 +140,8 @@ def test_gpu_built_uneven_leaves_meet_the_tolerance(name):
     ro = P.dyadic_leaves(c["om"], -N / 2, N / 2, L)
     co = P.dyadic_leaves(c["xs"], 0.0, 1.0, L)
     assert np.array_equal(ro, c["ro"]) and np.array_equal(co, c["co"])
-    plan = P.Plan.build_leaves(c["om"], c["xs"], L, ro, co, eps=eps, kernel="dft", sign=-1)
+    plan = P.Plan.build_leaves(c["om"], c["xs"], L, ro, co, eps=eps, kernel="dft", sign=-1,
+                               qr_arith=P.QR_DF64 if name == "nufft_1000" else P.QR_FP64)
     st = plan.stats()
     assert st["n0"] == 0 and st["N"] == N and st["rank_saturated"] == 0
     g = inputs.complex_gaussian(N, 2, seed=6)
