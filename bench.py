@@ -566,13 +566,18 @@ def sub_autograd(plan, P, torch, inputs, steps, warmup, world, lpk, R=32):
     value, tmax = job_throughput(1.0, sec, world)
     fma_pk = lpk["fp32_tflops"] / 2
     achieved = 8.0 * plan.stats()["entries"] * R / sec / 1e12  # forward + adjoint: 4 real FMA per entry and rhs each
+    hbm_pk, hbm_kind = peaks()
+    lbytes = 2 * plan.level_bytes(R, 8, 8)  # forward and adjoint, one launch per level each
     lg = N.bit_length() - 1
     return {"metric": f"IDBF forward+backward steps/s at N=2^{lg}, {R} RHS (loss ||Kx-b||^2, adjoint-butterfly backward)",
             "value": value, "unit": "fwd+bwd/s", "ms_per_step": tmax * 1e3, "steps": steps, "dtype": "f32",
             "workload": f"1D FIO N=2^{lg} eps=1e-6 leaf 64, {R} RHS complex64 (x seed 5, b seed 6)",
             "loss": float(out["loss"].detach()), "grad_norm": float(torch.linalg.norm(out["g"])),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fma_pk, "unit": "TFMA/s", "frac": achieved / fma_pk,
-                         "peak_kind": "measured in this run: cuBLAS SGEMM 8192^3 (FP32, TF32 off) / 2 flops per FMA"},
+                         "peak_kind": "measured in this run: cuBLAS SGEMM 8192^3 (FP32, TF32 off) / 2 flops per FMA",
+                         "hbm": {"achieved": lbytes / sec / 1e9, "peak": hbm_pk, "unit": "GB/s",
+                                 "frac": lbytes / sec / 1e9 / hbm_pk, "peak_kind": hbm_kind,
+                                 "bytes_per_step": lbytes}},
             "gradient_checks": "finite differences, dense K^* and gradcheck at N=4096 (tests/test_gpu_autograd.py)"}
 
 
@@ -605,6 +610,8 @@ def sub_mrhs(P, torch, inputs, log2n, steps, warmup, world, lpk, R=256):
                      "rel_err_vs_fp64": float(torch.linalg.norm(yb.to(torch.complex128) - y64) / nrm),
                      "speedup_vs_fp64": s64 / sec}
     st = plan.stats()
+    lbytes = plan.level_bytes(R, 8, 8)     # complex64 factors and vectors
+    hbm_pk, hbm_kind = peaks()
     useful = 8.0 * st["entries"] * R       # real flops of the complex block products
     executed = 3.0 * useful                # three split products on the tensor cores
     stc = res["tf32x3"]["ms_per_apply"] / 1e3
@@ -616,10 +623,17 @@ def sub_mrhs(P, torch, inputs, log2n, steps, warmup, world, lpk, R=256):
                                           "complex64 factors",
             "rel_err_vs_fp64": res["tf32x3"]["rel_err_vs_fp64"], "bar": "eps + 1e-6 = 2e-6",
             "vector_applies_per_s": value * R, "fp64_ms_per_apply": s64 * 1e3, "modes": res,
-            "roofline": {"bound": "tensor", "achieved": executed / stc / 1e12, "unit": "TFLOP/s",
-                         "peak": lpk["tf32_tflops"], "frac": executed / stc / 1e12 / lpk["tf32_tflops"],
-                         "peak_kind": "measured in this run: cuBLAS TF32 GEMM 8192^3",
-                         "useful_TFLOPs": useful / stc / 1e12}}
+            # one launch per level: each reads its input boundary and writes its output boundary
+            # (3.1 GB each at 256 right-hand sides), which outweighs the 5.5 GB of factors; the
+            # tensor work (3 split products) would take 4.3 ms at the measured TF32 rate, the bytes
+            # ~13 ms at the measured HBM rate: HBM is the bound of this unfused form
+            "roofline": {"bound": "hbm", "achieved": lbytes / stc / 1e9, "unit": "GB/s", "peak": hbm_pk,
+                         "frac": lbytes / stc / 1e9 / hbm_pk, "peak_kind": hbm_kind,
+                         "bytes_per_apply": lbytes, "traffic": None,
+                         "tensor": {"achieved": executed / stc / 1e12, "unit": "TFLOP/s", "peak": lpk["tf32_tflops"],
+                                    "frac": executed / stc / 1e12 / lpk["tf32_tflops"],
+                                    "peak_kind": "measured in this run: cuBLAS TF32 GEMM 8192^3",
+                                    "useful_TFLOPs": useful / stc / 1e12}}}
 
 
 def sub_batch(P, torch, inputs, cap_log2n, steps, warmup, world, lpk):

@@ -377,6 +377,8 @@ typedef struct {
   int64_t device_bytes;                    /* device memory held by the plan */
   int32_t level_variant[3][IDBF_MAX_LEVELS]; /* forward kernel per storage format and level (-1: default) */
   uint32_t level_storage[IDBF_MAX_LEVELS];   /* storage formats held by level l (bit IDBF_STORE_*) */
+  int64_t boundary_entries[IDBF_MAX_LEVELS]; /* summed segment lengths of boundary b = 0..L-1 (the
+                                                vector entries level b writes and level b+1 reads) */
 } idbf_stats_t;
 
 /* idbf_stats - fill *s (host memory). Synchronous, no GPU work. */

@@ -210,13 +210,20 @@ class Plan:
                     level_kmax=list(s.level_kmax[:nl]), segment_entries=s.segment_entries,
                     build_seconds=s.build_seconds, device_bytes=s.device_bytes,
                     level_variant={f: list(s.level_variant[f][:nl]) for f in range(3)},
-                    level_storage=list(s.level_storage[:nl]))
+                    level_storage=list(s.level_storage[:nl]),
+                    boundary_entries=list(s.boundary_entries[:s.L]))
 
     def algorithmic_bytes(self, nrhs: int = 1, entry_bytes: int = 16, vec_bytes: int = 16) -> int:
         """Bytes one apply must move at least: every stored factor entry once, the int32
         skeleton / redundant indices once, x read and y written."""
         st = self.stats()
         return st["entries"] * entry_bytes + st["index_entries"] * 4 + 2 * self.N * nrhs * vec_bytes
+
+    def level_bytes(self, nrhs: int = 1, entry_bytes: int = 16, vec_bytes: int = 16) -> int:
+        """Bytes of one apply run level by level (one launch per level): algorithmic_bytes plus
+        every intermediate boundary written by one level and read by the next."""
+        st = self.stats()
+        return self.algorithmic_bytes(nrhs, entry_bytes, vec_bytes) + 2 * sum(st["boundary_entries"]) * nrhs * vec_bytes
 
     def close(self):
         if self._h is not None and self._h.value:

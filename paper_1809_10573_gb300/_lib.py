@@ -47,7 +47,8 @@ class Stats(C.Structure):
                 ("level_entries", C.c_int64 * MAX_LEVELS), ("level_kmin", C.c_int32 * MAX_LEVELS),
                 ("level_kmax", C.c_int32 * MAX_LEVELS), ("segment_entries", C.c_int64),
                 ("build_seconds", C.c_double), ("device_bytes", C.c_int64),
-                ("level_variant", (C.c_int32 * MAX_LEVELS) * 3), ("level_storage", C.c_uint32 * MAX_LEVELS)]
+                ("level_variant", (C.c_int32 * MAX_LEVELS) * 3), ("level_storage", C.c_uint32 * MAX_LEVELS),
+                ("boundary_entries", C.c_int64 * MAX_LEVELS)]
 
 
 _lib = None

@@ -578,6 +578,7 @@ idbf_status idbf_stats(idbf_plan h, idbf_stats_t* s) {
   for (int l = 0; l <= p.L && l < IDBF_MAX_LEVELS; ++l)
     for (int f = 0; f < 3; ++f)
       if (p.lmat[f][l] || p.lmat_len[l] == 0) s->level_storage[l] |= 1u << f;
+  for (int b = 0; b < p.L && b < IDBF_MAX_LEVELS; ++b) s->boundary_entries[b] = p.seg_total[b];
   return IDBF_OK;
 }
 

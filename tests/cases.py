@@ -15,6 +15,9 @@ CASES = {
     "fio_paper_2048": (2048, 8, ("fio", 0, 1), "uniform", 1e-6, {}),                # Example 1, L = 8
     "fio_base_8192_oddL": (8192, 64, ("fio", 0, 0), "uniform", 1e-6, dict(t=2, t_leaf=4)),  # L = 7
     "j0_2048": (2048, 16, ("j0", 0, 0), "schlomilch", 1e-8, dict(t=2, t_leaf=4)),   # Example 2, L = 7
+    # the benchmark's FIO at N = 2^14 (L = 8): 256 nodes per level, blocks of up to 181 rows and
+    # 324 columns, the tall shapes of the N = 2^20 benchmark's middle levels
+    "fio_base_16384": (16384, 64, ("fio", 0, 0), "uniform", 1e-6, dict(t=2, t_leaf=4)),
 }
 
 

@@ -143,7 +143,7 @@ def test_ctypes_structures_match_the_c_layout(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     checks = [("idbf_stats_t", _lib.Stats, ["entries", "segment_entries", "device_bytes", "level_variant",
-                                            "level_storage"]),
+                                            "level_storage", "boundary_entries"]),
               ("idbf_params", _lib.Params, ["leaf", "seed", "qr_arith"]),
               ("idbf_host_factors", _lib.HostFactors, ["seg_len", "mat_len", "idx_len", "col_leaf_off"]),
               ("idbf_kernel", _lib.Kernel, ["c_profile"])]

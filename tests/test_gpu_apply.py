@@ -46,7 +46,7 @@ def test_fp64_apply_and_adjoint_match_oracle(case, nrhs):
     assert rel(ya, idbf.apply_adjoint(c["F"], X)) < 1e-12
 
 
-@pytest.mark.parametrize("case", ["dft_1024", "fio_base_4096", "fio_base_8192_oddL"])
+@pytest.mark.parametrize("case", ["dft_1024", "fio_base_4096", "fio_base_8192_oddL", "fio_base_16384"])
 @pytest.mark.parametrize("nrhs", [1, 6])
 def test_df64_apply_and_adjoint_match_oracle(case, nrhs):
     c, plan = _plan(case, P.STORE_DF64)
@@ -157,7 +157,7 @@ def test_bounded_waits_report_a_timeout_and_the_context_survives():
     assert rel(y.cpu().numpy(), idbf.apply(c["F"], X)) < 1e-12
 
 
-@pytest.mark.parametrize("case", ["fio_base_8192_oddL", "dft_jit_2048_oddL"])
+@pytest.mark.parametrize("case", ["fio_base_8192_oddL", "dft_jit_2048_oddL", "fio_base_16384"])
 @pytest.mark.parametrize("mode,fmt,tol", [(P.MODE_DF64, P.STORE_DF64, 1e-12), (P.MODE_FP32, P.STORE_C64, 2e-5),
                                           (P.MODE_FP64, P.STORE_C128, 1e-12)])
 def test_every_forward_variant_matches_oracle(case, mode, fmt, tol):

@@ -5,8 +5,8 @@ hi*hi + hi*lo + lo*hi accumulate in FP32, so a block product is about as accurat
 one. The bar is the one stated for the split-FP32 tensor form: relative 2-norm error at most
 eps + 1e-6 against the oracle's FP64 apply of the same factors (the factorization error eps does
 not even enter this comparison, so the bar is met with eps to spare). Cases: eps = 1e-6 FIO
-(Example 1 kernel of the benchmark) at N = 8192 with blocks of up to 162 rows (three 64-row
-passes of the tensor-core tile), full 128-RHS tiles and ragged ones, the jittered DFT and the
+(Example 1 kernel of the benchmark) at N = 16384 and 8192 with blocks of up to 181 and 162 rows
+(three 64-row passes of the tensor-core tile), full 128-RHS tiles and ragged ones, the jittered DFT and the
 paper's FIO at eps = 1e-6, and two eps = 1e-8 cases.
 
 IDBF_MODE_TF32X3_S64 applies the middle factor S^h in double-float or FP64 on the CUDA cores
@@ -33,7 +33,8 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
-CASES_TC = [("fio_base_8192_oddL", 256), ("fio_base_8192_oddL", 61), ("fio_base_8192_oddL", 160),
+CASES_TC = [("fio_base_16384", 256), ("fio_base_16384", 100), ("fio_base_8192_oddL", 256), ("fio_base_8192_oddL", 61),
+            ("fio_base_8192_oddL", 160),
             ("dft_jit_2048_oddL", 256), ("fio_paper_2048", 130), ("fio_base_4096", 256), ("dft_1024", 5),
             ("dft_1024", 130)]
 
