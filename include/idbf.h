@@ -184,10 +184,11 @@ typedef struct {
  * every segment is non-empty. With leaf offsets (Example 3: random points, coordinate-based
  * trees), N is any size >= 1, n0 is ignored (0), leaves and segments may be empty, and blocks
  * with no columns contribute zeros. Plans with leaves of uneven size run the per-node level
- * kernels only (FP64, double-float and FP32, any number of right-hand sides, forward and
- * adjoint, idbf_apply_noalloc): the streaming, warp, register-tiled and tensor-core kernels,
- * batches and checkpoints refuse them with EUNSUPPORTED. Offsets that are all equal are the
- * uniform case. Synchronous. */
+ * kernels (FP64, double-float and FP32, any number of right-hand sides, forward and adjoint,
+ * idbf_apply_noalloc) and, for one right-hand side, the streaming kernels and fused level
+ * pairs; the warp-per-node, register-tiled and tensor-core kernels, batches and checkpoints
+ * refuse them (EUNSUPPORTED; an apply then uses the per-node kernel). Offsets that are all equal
+ * are the uniform case. Synchronous. */
 idbf_status idbf_import_factors(const idbf_host_factors* f, int32_t storage, void* stream,
                                 idbf_plan* out);
 

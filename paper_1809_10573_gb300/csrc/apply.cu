@@ -402,8 +402,8 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       NodeMeta m;
       m.j = jj;
       m.sel = 0;
-      m.in0 = dl.lev == 0 ? 0 : dl.in_off[2 * jj];
-      m.l0 = dl.lev == 0 ? dl.n0 : dl.in_len[2 * jj];
+      m.in0 = dl.lev == 0 ? leaf_start(dl, jj) : dl.in_off[2 * jj];  // level 0: the leaf's first row of x
+      m.l0 = dl.lev == 0 ? leaf_len(dl, jj) : dl.in_len[2 * jj];
       m.l1 = dl.lev == 0 ? 0 : dl.in_len[2 * jj + 1];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
@@ -446,7 +446,6 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     NodeMeta nxt = meta(un < nunits ? un : 0, 0);
     for (; un < nunits && ok; ++nn) {
       const NodeMeta cur = nxt;
-      const int64_t j = cur.j;
       const bool second = PAIR && cur.sel;
       const DevLevel& dl = second ? d1 : d;
       const typename P::mat_t* ml = second ? mat1 : mat;
@@ -462,8 +461,8 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       if (second) {
         // inputs already in shared memory (mid)
       } else if (dl.lev == 0) {
-        usrc = (const unsigned char*)(io.x + j * dl.n0);
-        ubytes = inputs_bulk ? (uint32_t)(dl.n0 * VS) : 0;
+        usrc = (const unsigned char*)(io.x + cur.in0);
+        ubytes = inputs_bulk ? (uint32_t)(cur.l0 * VS) : 0;
       } else {
         usrc = (const unsigned char*)(io.win + cur.in0);
         ubytes = inputs_bulk ? (uint32_t)((cur.l0 + cur.l1) * VS) : 0;
@@ -544,7 +543,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     const bool to_mid = PAIR && sub < 2;    // level l of a pair: outputs to mid
     const int kind = second ? d1.kind : d.kind;
     const int lev = second ? d1.lev : d.lev;
-    const int Lv = d.L, n0 = d.n0;
+    const int Lv = d.L;
     const int32_t* lidx = second ? d1.idx : d.idx;
     const int64_t j = nm.j;
     const int l0 = failed ? 0 : nm.l0, l1 = failed ? 0 : nm.l1;
@@ -562,12 +561,12 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     if (second) {
       u = mid + in0;
     } else {
-      const uintptr_t usrc = lev == 0 ? (uintptr_t)(io.x + j * n0) : (uintptr_t)(io.win + in0);
+      const uintptr_t usrc = lev == 0 ? (uintptr_t)(io.x + in0) : (uintptr_t)(io.win + in0);
       u = ubuf + (size_t)b * geo.ucap + (int)((usrc & 15) / VS);
       if (!inputs_bulk) {  // plain loads by the consumers
         V* uw = ubuf + (size_t)b * geo.ucap;
         if (lev == 0) {
-          for (int i = tc; i < l0; i += NCT) uw[i] = io.x[j * n0 + i];
+          for (int i = tc; i < l0; i += NCT) uw[i] = io.x[in0 + i];
         } else {
           const V* src = io.win + in0;
           for (int i = tc; i < l0 + l1; i += NCT) uw[i] = src[i];
@@ -706,6 +705,14 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       if (kind == KIND_V && cols == 0 && !failed) {  // all skeleton: out = u[q]
         for (int r = tc; r < rows; r += NCT) outp[ob + r] = u[ix[r]];
       }
+      // a block with rows but no columns (an empty node of a coordinate-based tree) multiplies
+      // nothing: its product is zero (row IDs: block 0 sets t[p_0], block 1 adds nothing)
+      if (rows > 0 && cols == 0 && !failed) {
+        if (kind == KIND_S)
+          for (int r = tc; r < rows; r += NCT) outp[ob + r] = P::zero();
+        else if (kind == KIND_U && c == 0)
+          for (int r = tc; r < rows; r += NCT) t[ix[l0 + r]] = P::zero();
+      }
       consumer_sync<NCT>();  // red is reused by the next block; t must be complete before c = 1
     }
     // the node's inputs and index lists are no longer read: release the buffer
@@ -719,7 +726,8 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       consumer_sync<NCT>();
       if (*(volatile int*)&cons_abort) break;
       if (lev == Lv) {
-        for (int i = tc; i < tl; i += NCT) io.y[j * n0 + i] = t[i];
+        const int64_t y0 = second ? leaf_start(d1, j) : leaf_start(d, j);
+        for (int i = tc; i < tl; i += NCT) io.y[y0 + i] = t[i];
       } else {
         for (int i = tc; i < tl; i += NCT) outp[i < olen0 ? obv[0] + i : obv[1] + (i - olen0)] = t[i];
       }
@@ -797,7 +805,10 @@ static idbf_status launch_stream(Plan* p, int l, bool pair, bool bulk, bool spli
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t units = pair ? p->m / 2 : p->m;
   const unsigned ctas = (unsigned)std::min<int64_t>(units, (int64_t)RG::CTAS * sms);
-  const int x_ok = ((uintptr_t)x % 16 == 0) && ((p->n0 * (int)sizeof(V)) % 16 == 0);
+  // bulk copies of the level-0 inputs read whole 16-byte granules: every leaf of x must start and
+  // end on one (uneven leaves: only with 16-byte elements), else the consumers load them
+  const int x_ok = ((uintptr_t)x % 16 == 0) &&
+                   (p->uneven ? sizeof(V) % 16 == 0 : (p->n0 * (int)sizeof(V)) % 16 == 0);
   const int use_bulk = bulk && (l > 0 || x_ok);
   const DevLevel d = p->level(l);
   const DevLevel d1 = p->level(pair ? l + 1 : l);
@@ -852,7 +863,7 @@ static idbf_status launch_fwd_variant(Plan* p, int l, int v, const void* x, void
   IO<V> io;
   io.x = (const V*)x; io.ldx = p->N; io.y = (V*)y; io.ldy = p->N; io.R = 1;
   io.win = win; io.wout = wout;
-  if (v != 0 && p->uneven) return IDBF_EUNSUPPORTED;  // uneven leaves: the per-node kernel only
+  if (v == 7 && p->uneven) return IDBF_EUNSUPPORTED;  // uneven leaves: per-node and streaming kernels
   if (v == 7) return launch_warp_node<P>(p, l, io, st, fmt);
   if (v != 0 && fmt == IDBF_STORE_C128) return IDBF_EUNSUPPORTED;  // FP64: per-node or warp-per-node kernel
   if (v >= kFirstPairVariant) {  // levels l and l + 1 fused (win: boundary l - 1, wout: boundary l + 1)
@@ -913,8 +924,7 @@ static idbf_status run_fwd1(Plan* p, const void* x, void* y, int64_t ld, cudaStr
   V* wb[2] = {(V*)p->d_ws, (V*)((char*)p->d_ws + (size_t)p->max_seg_total * 16)};
   int cur = 1;  // buffer holding the last boundary written (boundary b in b % 2 without pairs)
   for (int l = 0; l <= p->L;) {
-    int v = p->uneven ? 0
-            : p->tuned[fmt].size() > (size_t)l && p->tuned[fmt][l] >= 0 ? p->tuned[fmt][l] : default_variant(fmt);
+    int v = p->tuned[fmt].size() > (size_t)l && p->tuned[fmt][l] >= 0 ? p->tuned[fmt][l] : default_variant(fmt);
     const bool pair = is_pair_variant(v) && l < p->L;
     const int last = pair ? l + 1 : l;  // level whose outputs this launch writes
     const V* win = l > 0 ? wb[cur] : nullptr;

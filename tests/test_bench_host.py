@@ -84,6 +84,15 @@ def test_level_variants_option_parsing():
         bench.parse_level_variants("df64=7,x")
 
 
+def test_launches_per_apply_counts_fused_pairs_once():
+    # a pair variant (16-19) on level l < L covers levels l and l + 1; on level L it is one level
+    assert bench.launches_per_apply([1] * 15, 14) == 15
+    assert bench.launches_per_apply([19, 19, 14, 1, 1, 1, 1, 5, 1, 10, 14], 10) == 10
+    assert bench.launches_per_apply([16, 3, 17, 0, 1], 4) == 3
+    assert bench.launches_per_apply([0, 1, 16], 2) == 3
+    assert bench.launches_per_apply([0, 16, 16], 2) == 2
+
+
 def test_oracle_team_times_one_core_then_all(monkeypatch):
     """The CPU baseline's worker processes (spawned: no CUDA state is inherited) build the oracle's
     factorization, then run the single-core and the all-core phases in lockstep with the parent."""

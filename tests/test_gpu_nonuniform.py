@@ -98,19 +98,36 @@ def test_uneven_leaves_against_the_dense_sum():
         assert rel(y, idbf.dense_matvec(c["K"], c["om"], c["xs"], g)) < 10 * c["eps"]
 
 
-def test_uneven_leaves_run_the_per_node_kernels_only():
+@pytest.mark.parametrize("name", ["nufft_3000_oddL", "clustered_640", "clustered_48_exact"])
+@pytest.mark.parametrize("mode,store,dt,bar", MODES[1:], ids=["df64", "fp32"])
+def test_uneven_leaves_every_forward_variant(name, mode, store, dt, bar):
+    """Uneven and empty leaves through every single-vector forward variant (the streaming kernel
+    with its ring layouts and fused level pairs reads leaf offsets and writes zero products for
+    blocks without columns; the warp-per-node kernel is refused and falls back), and through the
+    autotuner's choice."""
+    c = case(name)
+    plan = P.Plan.import_factors(c["ex"], storage=store)
+    X = inputs.complex_gaussian(c["N"], 1, seed=4)
+    xd = torch.from_numpy(X).to(dt).cuda()
+    ref = idbf.apply(c["F"], xd.cpu().numpy().astype(np.complex128))
+    L = c["ex"]["L"]
+    for v in range(P.NUM_FWD_VARIANTS):
+        for pat in [[v] * (L + 1)] + ([[1] + [v] * L] if v >= 16 else []):
+            plan.set_level_variants(mode, pat)
+            y = plan.apply(xd, mode=mode)
+            plan.sync_status()
+            assert rel(y.cpu().numpy(), ref) < bar, f"variant {v}, pattern {pat}"
+    plan.autotune(mode, reps=1)
+    assert rel(plan.apply(xd, mode=mode).cpu().numpy(), ref) < bar
+
+
+def test_uneven_leaves_refuse_the_tensor_cores_and_batches():
     c = case("nufft_1000")
-    plan = P.Plan.import_factors(c["ex"], storage=P.STORE_C128)
-    plan.set_storage(P.STORE_C128, P.STORE_DF64, P.STORE_C64)
-    g = torch.from_numpy(inputs.complex_gaussian(c["N"], 1, seed=4)[:, 0]).cuda()
-    ref = plan.apply(g, mode=P.MODE_DF64).cpu().numpy()
-    plan.autotune(P.MODE_DF64, reps=1)   # every variant but the per-node kernel is refused
-    assert set(plan.stats()["level_variant"][P.STORE_DF64]) == {0}
-    assert rel(plan.apply(g, mode=P.MODE_DF64).cpu().numpy(), ref) == 0.0
+    plan = P.Plan.import_factors(c["ex"], storage=P.STORE_C64)
     with pytest.raises(P.IDBFError):
         plan.apply(torch.zeros((c["N"], 4), dtype=torch.complex64, device="cuda"), mode=P.MODE_TF32X3)
     with pytest.raises(P.IDBFError):
-        P.Batch([plan], [1], mode=P.MODE_DF64)
+        P.Batch([plan], [1], mode=P.MODE_FP32)
 
 
 def test_uneven_leaves_allocation_free_apply():
