@@ -554,6 +554,8 @@ def _gpu_headline(args, rank, world, np, torch, P, inputs, team):
         torch.cuda.empty_cache()
         configs["batch"] = sub_batch(P, torch, inputs, None, max(3, min(args.steps, 5)), args.warmup, world, lpk)
         torch.cuda.empty_cache()
+        configs.update(sub_examples(P, torch, inputs, N_LOG2, sub_steps, args.warmup, world, lpk))
+        torch.cuda.empty_cache()
     line["configs"] = configs
     if team is not None:
         times = team.run()
@@ -762,6 +764,82 @@ def sub_build(P, torch, inputs, log2n, lpk, arith=("fp64", "df64")):
     return out
 
 
+def sub_examples(P, torch, inputs, log2n, steps, warmup, world, lpk):
+    """The paper's other two workloads at N = 2^log2n, built on the GPU (double-float QR) and
+    applied to one vector: Example 2, the Schloemilch expansion J_0(x xi) on x_k = (k-1)/N,
+    xi_n = n pi; Example 3, the non-uniform DFT exp(-2 pi i omega x) on N random omega in
+    [-N/2, N/2) and N random x in [0, 1), on coordinate-based dyadic trees (leaves of uneven size,
+    about 64 points each). Per example: build seconds, stored entries, eps^a of Sec. 3 on 256 rows
+    against GPU direct rows (FP64 apply), and the double-float and FP32 applies (autotuned per
+    level) with their errors against the FP64 apply and their HBM figures: algorithmic bytes
+    (factors, indices, x and y once) and level bytes (plus each boundary written and read back)
+    per second, against the measured copy bandwidth."""
+    import numpy as np
+    N = 1 << log2n
+    hbm_pk, hbm_kind = peaks()
+    out = {}
+    g = torch.from_numpy(inputs.complex_gaussian(N, 1, seed=SEED)[:, 0]).cuda()
+    g32 = g.to(torch.complex64)
+    rows = torch.from_numpy(inputs.sample_rows(N, 256, seed=SEED)).cuda()
+    for name in ("ex2_schlomilch_j0", "ex3_nufft_random_points"):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        if name.startswith("ex2"):
+            x, xi = inputs.schlomilch_grid(N)
+            kern, sign = "j0", -1
+            # J_0 needs more sampled rows than the FIO for the same accuracy (t = 2 gives eps^a
+            # ~18 eps at N = 2^20, t = 4 ~5 eps, at the same ranks)
+            plan = P.Plan.build(x, xi, eps=EPS, leaf=LEAF, kernel=kern, oversample=2 * T_OVERSAMPLE,
+                                oversample_leaf=2 * T_LEAF, qr_arith=P.QR_DF64)
+            desc = (f"Example 2: J_0(x xi), x_k=(k-1)/N, xi_n=n pi, N=2^{log2n}, eps=1e-6, leaf 64, "
+                    f"Mock-Chebyshev t=4 (t=8 at the leaf)")
+        else:
+            x, xi = inputs.nufft_points(N, seed=N)   # x: the row points omega, xi: the column points
+            kern, sign = "dft", -1
+            L = P.tree_depth(N, LEAF)
+            ro, co = P.dyadic_leaves(x, -N / 2, N / 2, L), P.dyadic_leaves(xi, 0.0, 1.0, L)
+            plan = P.Plan.build_leaves(x, xi, L, ro, co, eps=EPS, kernel=kern, sign=sign, oversample=T_OVERSAMPLE,
+                                       oversample_leaf=T_LEAF, qr_arith=P.QR_DF64)
+            desc = (f"Example 3: exp(-2 pi i omega x), N=2^{log2n} random omega in [-N/2,N/2) and x in [0,1) "
+                    f"(seed N), dyadic trees of depth {L}, leaves of uneven size (mean 64), eps=1e-6, "
+                    f"Mock-Chebyshev t=2 (t=4 at the leaf)")
+        torch.cuda.synchronize()
+        build_s = time.time() - t0
+        plan.set_storage(P.STORE_C128, P.STORE_DF64, P.STORE_C64)
+        st = plan.stats()
+        y64 = plan.apply(g, mode=P.MODE_FP64)
+        ud = P.kernel_matvec_rows(torch.from_numpy(np.ascontiguousarray(x)).cuda(),
+                                  torch.from_numpy(np.ascontiguousarray(xi)).cuda(), g, rows, kernel=kern, sign=sign)
+        eps_a = float(torch.linalg.norm(y64[rows] - ud) / torch.linalg.norm(ud))
+        nrm = torch.linalg.norm(y64)
+        modes = {}
+        for mname, mode, vec, eb in (("df64", P.MODE_DF64, g, 16), ("fp32", P.MODE_FP32, g32, 8)):
+            plan.autotune(mode, reps=10)
+            yb = torch.empty_like(vec)
+            sec = timed_loop(lambda: plan.apply(vec, mode=mode, out=yb), steps, warmup, world)
+            ab, lb = plan.algorithmic_bytes(1, eb, eb), plan.level_bytes(1, eb, eb)
+            modes[mname] = {"applies_per_s": 1.0 / sec, "ms_per_apply": sec * 1e3,
+                            "rel_err_vs_fp64": float(torch.linalg.norm(yb.to(torch.complex128) - y64) / nrm),
+                            "algorithmic_GBps": ab / sec / 1e9, "level_GBps": lb / sec / 1e9,
+                            "frac_of_hbm_algorithmic": ab / sec / 1e9 / hbm_pk,
+                            "level_variants": plan.stats()["level_variant"][P.STORE_DF64 if mname == "df64" else P.STORE_C64]}
+        s64 = timed_loop(lambda: plan.apply(g, mode=P.MODE_FP64), max(3, steps // 2), warmup, world)
+        modes["fp64"] = {"applies_per_s": 1.0 / s64, "ms_per_apply": s64 * 1e3}
+        value, tmax = job_throughput(1.0, modes["df64"]["ms_per_apply"] / 1e3, world)
+        out[name] = {"metric": f"IDBF applies/s, {name}, double-float, 1 RHS", "value": value, "unit": "applies/s",
+                     "ms_per_step": tmax * 1e3, "steps": steps, "dtype": "f32x2", "workload": desc,
+                     "build": {"seconds": build_s, "qr": "df64", "entries": st["entries"], "levels": st["L"] + 1,
+                               "level_kmax": st["level_kmax"], "device_GB": st["device_bytes"] / 1e9},
+                     "eps_a_fp64_vs_direct_256_rows": eps_a, "modes": modes,
+                     "roofline": {"bound": "hbm", "achieved": modes["df64"]["algorithmic_GBps"], "unit": "GB/s",
+                                  "peak": hbm_pk, "frac": modes["df64"]["frac_of_hbm_algorithmic"],
+                                  "peak_kind": hbm_kind, "traffic": None}}
+        plan.close()
+        del y64
+        torch.cuda.empty_cache()
+    return out
+
+
 def single_line(sub, args, world):
     """One JSON line for a workload run on its own (--workload mrhs | batch | autograd)."""
     line = {"metric": sub["metric"], "value": sub["value"], "unit": sub["unit"], "n_gpus": world,
@@ -788,6 +866,15 @@ def gpu_workload(args, rank, world):
         sub = sub_batch(P, torch, inputs, args.log2n, steps, args.warmup, world, lpk)
     elif args.workload == "build":
         sub = sub_build(P, torch, inputs, args.log2n if args.log2n is not None else 20, lpk)
+    elif args.workload == "examples":
+        subs = sub_examples(P, torch, inputs, args.log2n if args.log2n is not None else 20, steps, args.warmup, world,
+                            lpk)
+        if rank == 0:
+            for sub in subs.values():
+                line = single_line(sub, args, world)
+                line["library_peaks"] = lpk
+                print(json.dumps(line), flush=True)
+        return 0
     else:
         N = 1 << (args.log2n if args.log2n is not None else 20)
         x, xi = inputs.uniform_grid(N)
@@ -816,7 +903,7 @@ def main():
     ap.add_argument("--level-variants", default=None,
                     help="per-level forward variants instead of the autotuner, e.g. 'df64=7,1,10,...;fp32=...' "
                          "(apply workload)")
-    ap.add_argument("--workload", choices=["apply", "mrhs", "batch", "autograd", "build"], default="apply",
+    ap.add_argument("--workload", choices=["apply", "mrhs", "batch", "autograd", "build", "examples"], default="apply",
                     help="apply (default): the headline single-vector apply at N=2^20, with the multi-RHS, batch "
                          "and autograd workloads as sub-objects of its line; the others print a line of their own")
     ap.add_argument("--headline-only", action="store_true",
