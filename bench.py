@@ -653,9 +653,11 @@ def sub_mrhs(P, torch, inputs, log2n, steps, warmup, world, lpk, R=256):
 
 def sub_batch(P, torch, inputs, cap_log2n, steps, warmup, world, lpk):
     """Uneven batch: 64 operators, N = 2^e with e uniform in [12, 18], the first half the FIO and
-    the second half the jittered DFT kernel, 1-32 RHS each, eps = 1e-6, one persistent launch in a
-    CUDA graph, tiles autotuned. Timed in FP32 (the value) and double-float, each beside the same 64
-    applies made one plan at a time; errors against the FP64 apply. FIO operators of equal N are the
+    the second half the jittered DFT kernel, 1-32 RHS each, eps = 1e-6. Timed in FP32 (the value)
+    and double-float, each three ways: all 64 in one persistent launch in a CUDA graph (tiles
+    autotuned); with the split autotuned too (operators from some N up run through their own
+    per-level kernels after the launch; the value); and the same 64 applies made one plan at a
+    time. Errors against the FP64 apply. FIO operators of equal N are the
     same matrix: the first is built, the others are device copies of it (idbf_clone), so that every
     operator still reads factor memory of its own."""
     ops = inputs.uneven_batch(seed=4)
@@ -691,7 +693,16 @@ def sub_batch(P, torch, inputs, cap_log2n, steps, warmup, world, lpk):
         xm = [x.to(vdt) for x in xs]
         ym = [torch.empty_like(x) for x in xm]
         b = P.Batch(plans, [o["nrhs"] for o in ops], mode=mode)
-        tuned_ms = b.autotune(xm, reps=2)
+        # every operator in the one persistent launch (tiles autotuned)
+        reps = 1 if name == "df64" else 2  # a double-float trial takes ~1-2 s and repeats to 0.1 %
+        b.set_split(P.Batch.NO_SPLIT)
+        one_tuned = b.autotune(xm, reps=reps)
+        one = timed_loop(lambda: b.apply(xm, ym), steps, warmup, world)
+        one_tiles = b.info()
+        b.sync_status()
+        # the autotuner also chooses the size above which operators run through their own applies
+        b.set_split(0)
+        tuned_ms = b.autotune(xm, reps=reps)
         secs = timed_loop(lambda: b.apply(xm, ym), steps, warmup, world)
         b.sync_status()
         err = max(float(torch.linalg.norm(y.to(torch.complex128) - r) / torch.linalg.norm(r)) for y, r in zip(ym, y64))
@@ -700,9 +711,11 @@ def sub_batch(P, torch, inputs, cap_log2n, steps, warmup, world, lpk):
         fma = sum(4.0 * p.stats()["entries"] * x.shape[1] for p, x in zip(plans, xs))  # real FMA per complex MAC: 4
         res[name] = {"ms_per_batch": secs * 1e3, "batches_per_s": 1.0 / secs, "algorithmic_GBps": algo / secs / 1e9,
                      "useful_TFMA_per_s": fma / secs / 1e12,
-                     "algorithmic_bytes": algo, "max_rel_err_vs_fp64": err, "tiles": b.info(),
+                     "algorithmic_bytes": algo, "max_rel_err_vs_fp64": err, "tiles": b.info(), "split": b.split(),
                      "autotune_best_ms": tuned_ms, "separate_applies_ms": sep * 1e3,
-                     "speedup_vs_separate_applies": sep / secs}
+                     "speedup_vs_separate_applies": sep / secs,
+                     "one_launch": {"ms_per_batch": one * 1e3, "tiles": one_tiles, "autotune_best_ms": one_tuned,
+                                    "speedup_vs_separate_applies": sep / one}}
         b.close()
     for p in plans:
         p.close()
@@ -710,7 +723,8 @@ def sub_batch(P, torch, inputs, cap_log2n, steps, warmup, world, lpk):
     peak, kind = peaks()
     fma_pk = lpk["fp32_tflops"] / 2
     r32 = res["fp32"]
-    return {"metric": "IDBF uneven-batch applies/s (64 operators, N 2^12..2^18, 1-32 RHS, one persistent launch in a CUDA graph)",
+    return {"metric": "IDBF uneven-batch applies/s (64 operators, N 2^12..2^18, 1-32 RHS; one persistent launch in a "
+                      "CUDA graph for the operators below an autotuned size split, their own per-level launches above)",
             "value": value, "unit": "batches/s (64 operator applies each)", "ms_per_step": tmax * 1e3, "steps": steps,
             "dtype": "f32",
             "workload": "64 ops, seed 4: FIO (ops 0-31) / jittered DFT (32-63), eps=1e-6, leaf 64, complex64 factors"

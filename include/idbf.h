@@ -320,14 +320,17 @@ idbf_status idbf_batch_create(const idbf_plan* plans, int32_t nops, const int64_
 
 /* idbf_batch_apply - y[o] = K_o x[o] for every operator o (device pointers, column-major N_o x
  * nrhs[o] blocks with leading dimension ld[o] >= N_o, element type of `mode`): one graph launch
- * on `stream` after a small copy of the pointer table. */
+ * on `stream` after a small copy of the pointer table, then idbf_apply for each operator above
+ * the split (idbf_batch_set_split). */
 idbf_status idbf_batch_apply(idbf_batch b, const void* const* x, void* const* y, const int64_t* ld,
                              void* stream);
 
 /* idbf_batch_autotune - time the batch for every tiling of idbf_batch_set_tiling below (for the
  * mixed tiling 7 also its row threshold in {32, 64, 96, 128, 192}) and nodes per item in
- * {1, 2, 4} (reps launches each, on the given buffers; tilings whose shared memory exceeds
- * 200 KB are skipped) and keep the fastest; *best_ms receives its time per launch. Synchronous. */
+ * {1, 2, 4}, then, unless a split was set with idbf_batch_set_split, every split with the best
+ * tiling (and the tilings again if the split changed); reps launches each, on the given buffers;
+ * tilings whose shared memory exceeds 200 KB are skipped. Keeps the fastest; *best_ms receives
+ * its time per idbf_batch_apply. Synchronous. */
 idbf_status idbf_batch_autotune(idbf_batch b, const void* const* x, void* const* y, const int64_t* ld,
                                 int32_t reps, void* stream, float* best_ms);
 
@@ -341,13 +344,28 @@ idbf_status idbf_batch_autotune(idbf_batch b, const void* const* x, void* const*
  * previous tiling is then kept), IDBF_EINVAL for other values. Synchronous. */
 idbf_status idbf_batch_set_tiling(idbf_batch b, int32_t tile, int32_t nodes_per_item);
 
+/* idbf_batch_set_split - operators with N >= min_separate_n leave the persistent launch: each
+ * runs through idbf_apply (its own per-level kernels, stream-ordered after the launch) within
+ * idbf_batch_apply; INT64_MAX keeps every operator in the launch. Large operators fill the GPU
+ * by themselves, and without them the launch needs less shared memory per CTA. A split set here
+ * is kept by idbf_batch_autotune. min_separate_n = 0 (the state after idbf_batch_create) lets
+ * idbf_batch_autotune choose it among INT64_MAX and the N of each operator; until then every
+ * operator is in the launch. IDBF_EUNSUPPORTED if the remaining launch does not fit the current
+ * tiling (the previous split is then kept), IDBF_EINVAL for a negative value. This goes beyond
+ * the paper, which applies one operator at a time. Synchronous. */
+idbf_status idbf_batch_set_split(idbf_batch b, int64_t min_separate_n);
+
+/* idbf_batch_split - the current split and the number of operators applied through idbf_apply. */
+idbf_status idbf_batch_split(idbf_batch b, int64_t* min_separate_n, int32_t* separate_ops);
+
 /* idbf_batch_info - the current tiling: right-hand sides and nodes per work item, number of
- * items, persistent CTAs. */
+ * items, persistent CTAs (0 and 0 when every operator runs through idbf_apply). */
 idbf_status idbf_batch_info(idbf_batch b, int32_t* rhs_per_item, int32_t* nodes_per_item, int32_t* items,
                             int32_t* ctas);
 
 /* idbf_batch_sync_status - wait for `stream`; IDBF_ETIMEOUT if a bounded wait of the batch kernel
- * gave up since the last call (its results are invalid), IDBF_OK otherwise. */
+ * (or of an operator applied through idbf_apply) gave up since the last call (its results are
+ * invalid), IDBF_OK otherwise. */
 idbf_status idbf_batch_sync_status(idbf_batch b, void* stream);
 
 /* idbf_batch_debug_set_wait - fault injection for tests: set the time limit of the batch

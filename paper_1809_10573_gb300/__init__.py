@@ -290,6 +290,17 @@ class Batch:
     def set_tiling(self, tile: int, nodes_per_item: int = 1):
         _lib.check(_lib.lib().idbf_batch_set_tiling(self._h, int(tile), int(nodes_per_item)), "idbf_batch_set_tiling")
 
+    NO_SPLIT = (1 << 63) - 1  # idbf_batch_set_split: every operator in the persistent launch
+
+    def set_split(self, min_separate_n: int):
+        """Operators with N >= min_separate_n run through their own applies (idbf_batch_set_split)."""
+        _lib.check(_lib.lib().idbf_batch_set_split(self._h, int(min_separate_n)), "idbf_batch_set_split")
+
+    def split(self) -> dict:
+        n, k = C.c_int64(), C.c_int32()
+        _lib.check(_lib.lib().idbf_batch_split(self._h, C.byref(n), C.byref(k)), "idbf_batch_split")
+        return dict(min_separate_n=n.value, separate_ops=k.value)
+
     def debug_set_wait(self, limit_ns: int, extra_target: int = 0):
         """Fault injection for tests (idbf_batch_debug_set_wait in include/idbf.h)."""
         _lib.check(_lib.lib().idbf_batch_debug_set_wait(self._h, int(limit_ns), int(extra_target)),

@@ -87,6 +87,8 @@ SIGNATURES = {
     "idbf_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32)]),
     "idbf_batch_sync_status": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "idbf_batch_set_split": (C.c_int, [C.c_void_p, C.c_int64]),
+    "idbf_batch_split": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "idbf_batch_destroy": (None, [C.c_void_p]),
     "idbf_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "idbf_load": (C.c_int, [C.c_char_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),

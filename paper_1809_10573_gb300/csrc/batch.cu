@@ -185,6 +185,9 @@ struct idbf_batch_s {
   int ctas = 0;
   uint64_t limit_ns = 2000000000ull;
   int debug_extra = 0;  // fault injection: added to the first operator's level-0 completion target
+  int64_t split_n = INT64_MAX;  // operators with N >= split_n run through idbf_apply, not the launch
+  bool split_auto = true;       // idbf_batch_autotune chooses split_n
+  std::vector<char> sep;        // per operator: runs through idbf_apply
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;
@@ -235,9 +238,11 @@ size_t smem_for(idbf_batch_s* b) {
     return 0;
   } else {
     size_t sm = 0;
-    for (int o = 0; o < b->nops; ++o)
+    for (int o = 0; o < b->nops; ++o) {
+      if (b->sep[o]) continue;
       for (const LevelInfo& li : b->plans[o]->p.lv)
         sm = std::max(sm, bat::node_smem<P, RB, RPT, TC>(li, li.max_rows > b->mix_rows));
+    }
     return sm;
   }
 }
@@ -301,6 +306,8 @@ idbf_status layout(idbf_batch_s* b) {
   if (!tile_valid(b->mode, b->tile)) return IDBF_EUNSUPPORTED;
   b->rb = bat::kTiles[b->tile].rb;
   const bool mixed = bat::kTiles[b->tile].tc < 0;
+  b->sep.assign(b->nops, 0);
+  for (int o = 0; o < b->nops; ++o) b->sep[o] = b->plans[o]->p.N >= b->split_n ? 1 : 0;
   // level bodies of the mixed tiling (ignored by the others)
   for (int o = 0, li = 0; o < b->nops; ++o)
     for (const LevelInfo& lvi : b->plans[o]->p.lv) b->h_lv[li++].body = lvi.max_rows > b->mix_rows ? 1 : 0;
@@ -317,7 +324,7 @@ idbf_status layout(idbf_batch_s* b) {
   for (int l = 0; l <= maxL; ++l)
     for (int o = 0; o < b->nops; ++o) {
       const Plan& p = b->plans[o]->p;
-      if (l > p.L) continue;
+      if (l > p.L || b->sep[o]) continue;
       // the right-hand-side blocks of a run of nodes are neighbours in the queue, so the
       // blocks' second and later reads of the factors come from L2
       const int rbl = mixed && !b->h_lv[lbase[o] + l].body ? bat::kMixedSmallRB : b->rb;
@@ -337,6 +344,11 @@ idbf_status layout(idbf_batch_s* b) {
   b->nitems = (int)items.size();
   if (b->debug_extra > 0 && b->nlevels_total > 0) target[0] += b->debug_extra;
   if (!tile_valid(b->mode, b->tile)) return IDBF_EUNSUPPORTED;
+  if (b->nitems == 0) {  // every operator runs through idbf_apply: no persistent launch
+    b->smem = 0;
+    b->ctas = 0;
+    return IDBF_OK;
+  }
   b->smem = IDBF_BATCH_DISPATCH(smem_for, (size_t)0, b);
   if (b->smem == 0 || b->smem > 200 * 1024) return IDBF_EUNSUPPORTED;
   const int occ = IDBF_BATCH_DISPATCH(occupancy, 1, b);
@@ -459,9 +471,17 @@ idbf_status idbf_batch_apply(idbf_batch b, const void* const* x, void* const* y,
     memcpy(&tab[2 * b->nops + o], &ld[o], sizeof(int64_t));
   }
   cudaStream_t st = (cudaStream_t)stream;
-  // pageable source: the copy is staged before the call returns, so tab may go out of scope
-  IDBF_CUDA_TRY(cudaMemcpyAsync(b->d_ptrs, tab.data(), sizeof(void*) * tab.size(), cudaMemcpyHostToDevice, st));
-  IDBF_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+  if (b->exec) {
+    // pageable source: the copy is staged before the call returns, so tab may go out of scope
+    IDBF_CUDA_TRY(cudaMemcpyAsync(b->d_ptrs, tab.data(), sizeof(void*) * tab.size(), cudaMemcpyHostToDevice, st));
+    IDBF_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+  }
+  // the operators above the split: their own per-level kernels, after the persistent launch
+  for (int o = 0; o < b->nops; ++o) {
+    if (!b->sep[o]) continue;
+    const idbf_status s = idbf_apply(b->plans[o], x[o], y[o], b->R[o], ld[o], b->mode, stream);
+    if (s != IDBF_OK) return s;
+  }
   return IDBF_OK;
 }
 
@@ -474,38 +494,112 @@ idbf_status idbf_batch_autotune(idbf_batch b, const void* const* x, void* const*
   cudaEventCreate(&e1);
   float best = 1e30f;
   int btile = b->tile, bnpi = b->npi, bmix = b->mix_rows;
-  const int npis[3] = {1, 2, 4};
-  const int mixes[5] = {32, 64, 96, 128, 192};  // mixed tiling: row threshold of the per-thread body
+  int64_t bsplit = b->split_n;
   idbf_status s = IDBF_OK;
-  for (int a = 0; a < bat::kNumTiles && s == IDBF_OK; ++a)
-    for (int c = 0; c < 3 * 5 && s == IDBF_OK; ++c) {
-      if (!tile_valid(b->mode, a)) continue;
-      const bool mixed = bat::kTiles[a].tc < 0;
-      if (!mixed && c >= 3) continue;
-      b->tile = a;
-      b->npi = npis[c % 3];
-      b->mix_rows = mixed ? mixes[c / 3] : bmix;
-      idbf_status r = layout(b);
-      if (r == IDBF_EUNSUPPORTED) continue;
-      if (r != IDBF_OK) { s = r; break; }
-      if ((s = idbf_batch_apply(b, x, y, ld, stream)) != IDBF_OK) break;  // warm-up
-      cudaEventRecord(e0, st);
-      for (int k = 0; k < reps && s == IDBF_OK; ++k) s = idbf_batch_apply(b, x, y, ld, stream);
-      cudaEventRecord(e1, st);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= reps;
-      if (ms < best) { best = ms; btile = b->tile; bnpi = b->npi; bmix = b->mix_rows; }
+  // time the current layout (a warm-up launch, then reps launches); EUNSUPPORTED layouts are skipped
+  auto trial = [&]() {
+    idbf_status r = layout(b);
+    if (r == IDBF_EUNSUPPORTED) return;
+    if (r != IDBF_OK) { s = r; return; }
+    if ((s = idbf_batch_apply(b, x, y, ld, stream)) != IDBF_OK) return;
+    cudaEventRecord(e0, st);
+    for (int k = 0; k < reps && s == IDBF_OK; ++k) s = idbf_batch_apply(b, x, y, ld, stream);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (s == IDBF_OK && ms < best) {
+      best = ms;
+      btile = b->tile;
+      bnpi = b->npi;
+      bmix = b->mix_rows;
+      bsplit = b->split_n;
     }
+  };
+  // every tiling at the current split
+  auto tilings = [&]() {
+    const int npis[3] = {1, 2, 4};
+    const int mixes[5] = {32, 64, 96, 128, 192};  // mixed tiling: row threshold of the per-thread body
+    const int mix0 = bmix;
+    for (int a = 0; a < bat::kNumTiles && s == IDBF_OK; ++a)
+      for (int c = 0; c < 3 * 5 && s == IDBF_OK; ++c) {
+        if (!tile_valid(b->mode, a)) continue;
+        const bool mixed = bat::kTiles[a].tc < 0;
+        if (!mixed && c >= 3) continue;
+        b->tile = a;
+        b->npi = npis[c % 3];
+        b->mix_rows = mixed ? mixes[c / 3] : mix0;
+        trial();
+      }
+  };
+  if (b->split_auto) {
+    b->split_n = INT64_MAX;
+    bsplit = INT64_MAX;
+  }
+  tilings();
+  // then, with the best tiling, every split: all operators in the persistent launch, or those of
+  // N >= n for each N of the batch through their own per-level kernels; the tilings again if the
+  // best split changed
+  const int64_t split0 = bsplit;
+  if (s == IDBF_OK && b->split_auto) {
+    std::vector<int64_t> cand = {INT64_MAX};
+    for (const idbf_plan pl : b->plans) cand.push_back(pl->p.N);
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    for (const int64_t c : cand) {
+      if (s != IDBF_OK) break;
+      b->tile = btile;
+      b->npi = bnpi;
+      b->mix_rows = bmix;
+      b->split_n = c;
+      trial();
+    }
+  }
+  if (s == IDBF_OK && bsplit != split0) {
+    b->split_n = bsplit;
+    tilings();
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->tile = btile;
   b->npi = bnpi;
   b->mix_rows = bmix;
+  b->split_n = bsplit;
   if (s == IDBF_OK) s = layout(b);
   if (best_ms) *best_ms = best;
   return s;
+}
+
+idbf_status idbf_batch_set_split(idbf_batch b, int64_t min_separate_n) {
+  if (!b || min_separate_n < 0) return IDBF_EINVAL;
+  if (min_separate_n == 0) {  // the autotuner chooses; until then every operator stays in the launch
+    b->split_auto = true;
+    if (b->split_n == INT64_MAX) return IDBF_OK;
+    b->split_n = INT64_MAX;
+    return layout(b);
+  }
+  const int64_t old = b->split_n;
+  b->split_n = min_separate_n;
+  idbf_status s = layout(b);
+  if (s == IDBF_EUNSUPPORTED) {
+    b->split_n = old;
+    const idbf_status r = layout(b);
+    return r == IDBF_OK ? s : r;
+  }
+  b->split_auto = false;
+  return s;
+}
+
+idbf_status idbf_batch_split(idbf_batch b, int64_t* min_separate_n, int32_t* separate_ops) {
+  if (!b) return IDBF_EINVAL;
+  if (min_separate_n) *min_separate_n = b->split_n;
+  if (separate_ops) {
+    int32_t n = 0;
+    for (const char c : b->sep) n += c ? 1 : 0;
+    *separate_ops = n;
+  }
+  return IDBF_OK;
 }
 
 idbf_status idbf_batch_set_tiling(idbf_batch b, int32_t tile, int32_t nodes_per_item) {
@@ -547,11 +641,18 @@ idbf_status idbf_batch_sync_status(idbf_batch b, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   IDBF_CUDA_TRY(cudaMemcpyAsync(&v, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
   IDBF_CUDA_TRY(cudaStreamSynchronize(st));
+  idbf_status res = IDBF_OK;
   if (v) {
     IDBF_CUDA_TRY(cudaMemset(b->d_status, 0, sizeof(int)));
-    return IDBF_ETIMEOUT;
+    res = IDBF_ETIMEOUT;
   }
-  return IDBF_OK;
+  // the operators applied through idbf_apply report their own bounded waits
+  for (int o = 0; o < b->nops; ++o) {
+    if (!b->sep[o]) continue;
+    const idbf_status r = idbf_sync_status(b->plans[o], stream);
+    if (r != IDBF_OK && res == IDBF_OK) res = r;
+  }
+  return res;
 }
 
 void idbf_batch_destroy(idbf_batch b) {

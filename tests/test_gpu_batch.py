@@ -67,6 +67,48 @@ def test_batch_matches_oracle_and_single_applies(mode, fmt, dt, tol):
     b.close()
 
 
+@pytest.mark.parametrize("mode,fmt,dt,tol", [(P.MODE_DF64, P.STORE_DF64, np.complex128, 1e-12),
+                                             (P.MODE_FP32, P.STORE_C64, np.complex64, 2e-5)])
+def test_batch_split_between_the_launch_and_separate_applies(mode, fmt, dt, tol):
+    """Operators of N >= the split run through their own applies after the persistent launch: at
+    every split (none, each N of the batch, all) the results match the oracle; with every operator
+    split off there is no launch at all."""
+    plans, xs, refs = [], [], []
+    for k, (case, r) in enumerate(CASES):
+        c = oracle_case(case)
+        plans.append(P.Plan.import_factors(c["ex"], storage=fmt))
+        X = inputs.complex_gaussian(c["N"], r, seed=50 + k)
+        xs.append(torch.from_numpy(X.astype(dt)).cuda())
+        refs.append(idbf.apply(c["F"], X))
+    b = P.Batch(plans, [r for _, r in CASES], mode=mode)
+    assert b.split() == dict(min_separate_n=P.Batch.NO_SPLIT, separate_ops=0)
+    Ns = sorted({p.N for p in plans})
+    for n in [P.Batch.NO_SPLIT] + Ns[::-1] + [1]:
+        b.set_split(n)
+        assert b.split()["separate_ops"] == sum(p.N >= n for p in plans)
+        if n == 1:
+            assert b.info()["items"] == 0 and b.info()["ctas"] == 0
+        for rep in range(2):
+            ys = b.apply(xs)
+            b.sync_status()
+            for y, ref in zip(ys, refs):
+                assert rel(y.cpu().numpy(), ref) < tol, (n, rep)
+    with pytest.raises(P.IDBFError):
+        b.set_split(-1)
+    b.set_split(Ns[-1])                        # a split set by hand is kept by the autotuner
+    b.autotune(xs, reps=1)
+    assert b.split()["min_separate_n"] == Ns[-1]
+    b.set_split(0)                             # the autotuner chooses
+    assert b.split()["min_separate_n"] == P.Batch.NO_SPLIT
+    ms = b.autotune(xs, reps=1)
+    assert ms > 0 and b.split()["min_separate_n"] in [P.Batch.NO_SPLIT] + Ns
+    ys = b.apply(xs)
+    b.sync_status()
+    for y, ref in zip(ys, refs):
+        assert rel(y.cpu().numpy(), ref) < tol
+    b.close()
+
+
 def test_batch_with_gpu_built_plans_of_uneven_size():
     plans, xs = [], []
     for k, (e, kind, r) in enumerate([(10, "fio", 2), (12, "dft", 9), (11, "fio", 1), (13, "dft", 4)]):
