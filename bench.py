@@ -694,16 +694,18 @@ def sub_batch(P, torch, inputs, cap_log2n, steps, warmup, world, lpk):
         ym = [torch.empty_like(x) for x in xm]
         b = P.Batch(plans, [o["nrhs"] for o in ops], mode=mode)
         # every operator in the one persistent launch (tiles autotuned)
-        reps = 1 if name == "df64" else 2  # a double-float trial takes ~1-2 s and repeats to 0.1 %
+        # a double-float batch takes 1-2 s and repeats to 0.1 %: fewer trials and steps there
+        reps = 1 if name == "df64" else 2
+        st_, wu_ = (min(steps, 3), min(warmup, 2)) if name == "df64" else (steps, warmup)
         b.set_split(P.Batch.NO_SPLIT)
         one_tuned = b.autotune(xm, reps=reps)
-        one = timed_loop(lambda: b.apply(xm, ym), steps, warmup, world)
+        one = timed_loop(lambda: b.apply(xm, ym), st_, wu_, world)
         one_tiles = b.info()
         b.sync_status()
         # the autotuner also chooses the size above which operators run through their own applies
         b.set_split(0)
         tuned_ms = b.autotune(xm, reps=reps)
-        secs = timed_loop(lambda: b.apply(xm, ym), steps, warmup, world)
+        secs = timed_loop(lambda: b.apply(xm, ym), st_, wu_, world)
         b.sync_status()
         err = max(float(torch.linalg.norm(y.to(torch.complex128) - r) / torch.linalg.norm(r)) for y, r in zip(ym, y64))
         sep = timed_loop(lambda: [p.apply(x, mode=mode) for p, x in zip(plans, xm)], max(1, steps // 2), 1, world)
