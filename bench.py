@@ -696,7 +696,7 @@ def sub_batch(P, torch, inputs, cap_log2n, steps, warmup, world, lpk):
         # every operator in the one persistent launch (tiles autotuned)
         # a double-float batch takes 1-2 s and repeats to 0.1 %: fewer trials and steps there
         reps = 1 if name == "df64" else 2
-        st_, wu_ = (min(steps, 3), min(warmup, 2)) if name == "df64" else (steps, warmup)
+        st_, wu_ = (min(steps, 3), min(warmup, 3)) if name == "df64" else (steps, warmup)
         b.set_split(P.Batch.NO_SPLIT)
         one_tuned = b.autotune(xm, reps=reps)
         one = timed_loop(lambda: b.apply(xm, ym), st_, wu_, world)
