@@ -313,8 +313,10 @@ typedef struct idbf_batch_s* idbf_batch;
  * CUDA graph (plans with leaves of n0 points; uneven leaves: EUNSUPPORTED). Work items
  * (operator, level, run of nodes, block of right-hand sides) are queued in
  * level order and taken by persistent CTAs; an item waits (bounded) until the previous level of
- * its operator is complete. Allocates each operator's level workspace; the plans must outlive
- * the batch and must not be changed (storage) while it exists. Synchronous. */
+ * its operator is complete. Operators from a size up can be left out of the launch and applied
+ * on their own (idbf_batch_set_split, chosen by idbf_batch_autotune). Allocates each operator's
+ * level workspace; the plans must outlive the batch and must not be changed (storage) while it
+ * exists. Synchronous. */
 idbf_status idbf_batch_create(const idbf_plan* plans, int32_t nops, const int64_t* nrhs, int32_t mode,
                               idbf_batch* out);
 
