@@ -350,6 +350,9 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
   using V = typename P::vec_t;
   using G = typename P::gv_t;
   using M = typename P::mat_t;
+  // vectors between levels: the double-float policy keeps them in its own format (Bnd)
+  using BP = Bnd<P, std::is_same<P, DF64P>::value>;
+  using B = typename BP::b_t;
   constexpr int ES = (int)sizeof(M);
   constexpr int VS = (int)sizeof(V);
   constexpr int STAGES = RG::STAGES, STAGE_BYTES = RG::STAGE_BYTES;
@@ -363,6 +366,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
   int32_t* ibuf = (int32_t*)(smem + geo.ibuf_off);  // [2][icap]
   G* g = (G*)(smem + geo.g_off);
   V* t = (V*)(smem + geo.t_off);
+  B* tb = (B*)t;  // row-ID accumulator (U levels), in the boundary format
   typename P::part_t* red = (typename P::part_t*)(smem + geo.red_off);
   V* mid = (V*)(smem + geo.mid_off);                // level pairs: the four shared segments
   uint64_t* full = (uint64_t*)(smem + geo.bar_off);
@@ -556,6 +560,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     const int64_t mov[2] = {nm.mo[0], nm.mo[1]};
     const M* ml = second ? mat1 : mat;
     V* const outp = to_mid ? mid : io.wout;  // where this node's output segments go
+    B* const outb = (B*)outp;
     // inputs (shifted within 16 bytes of the copy) and index lists in shared memory
     const V* u;
     if (second) {
@@ -568,12 +573,17 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
         if (lev == 0) {
           for (int i = tc; i < l0; i += NCT) uw[i] = io.x[in0 + i];
         } else {
-          const V* src = io.win + in0;
-          for (int i = tc; i < l0 + l1; i += NCT) uw[i] = src[i];
+          const B* src = (const B*)(io.win + in0);
+          for (int i = tc; i < l0 + l1; i += NCT) ((B*)uw)[i] = src[i];
         }
         u = uw;
       }
     }
+    const B* ub = (const B*)u;  // the inputs of a level > 0 (and of the second level of a pair)
+    // gathered operand and pass-through term of input element e: level 0 converts x, later
+    // levels read the boundary format
+    auto gin = [&](int e) -> G { return lev == 0 ? P::cvt(u[e]) : BP::g_of(ub[e]); };
+    auto bin = [&](int e) -> B { return lev == 0 ? BP::of_v(u[e]) : ub[e]; };
     const int32_t* ix0 = nullptr;
     const int32_t* ix1 = nullptr;
     if (kind != KIND_S) {
@@ -596,13 +606,13 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
     // gathered operands: V: g = [u[p_0], u[p_1]]; S and U: g = u
     if (!failed) {
       if (kind == KIND_V) {
-        for (int i = tc; i < cols0; i += NCT) g[i] = P::cvt(u[ix0[rows0 + i]]);
-        for (int i = tc; i < cols1; i += NCT) g[cols0 + i] = P::cvt(u[ix1[rows1 + i]]);
+        for (int i = tc; i < cols0; i += NCT) g[i] = gin(ix0[rows0 + i]);
+        for (int i = tc; i < cols1; i += NCT) g[cols0 + i] = gin(ix1[rows1 + i]);
       } else {
-        for (int i = tc; i < l0 + l1; i += NCT) g[i] = P::cvt(u[i]);
+        for (int i = tc; i < l0 + l1; i += NCT) g[i] = gin(i);
       }
       if (kind == KIND_U)  // t[q_0] = in_0; t[p_0] comes from the block-0 products
-        for (int i = tc; i < l0; i += NCT) t[ix0[i]] = u[i];
+        for (int i = tc; i < l0; i += NCT) tb[ix0[i]] = bin(i);
     }
     consumer_sync<NCT>();
     const int tl = l0 + rows0;  // row-ID levels: |t| = |q_0| + |p_0|
@@ -611,7 +621,7 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       const int32_t* ix = c ? ix1 : ix0;
       const G* gc = g + (kind == KIND_S ? 0 : (kind == KIND_V ? c * cols0 : c * l0));
       if (kind == KIND_U && c == 1 && !failed) {  // block 0 has written all of t
-        for (int i = tc; i < l1; i += NCT) { V* q = &t[ix1[i]]; *q = P::add(*q, u[l0 + i]); }
+        for (int i = tc; i < l1; i += NCT) { B* q = &tb[ix1[i]]; *q = BP::add(*q, bin(l0 + i)); }
       }
       typename P::acc_t acc[RPT];
 #pragma unroll
@@ -693,25 +703,25 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
             for (int tm = 1; tm < TEAMS; ++tm)
               P::combine(acc[k], red[((SPLIT ? tm : tm - 1) * RPT + k) * TCT + tr]);
           }
-          const V v = P::fin(acc[k]);
+          const B v = BP::of_acc(acc[k]);
           if (kind == KIND_U) {
-            V* q = &t[ix[(c ? l1 : l0) + r]];
-            *q = c ? P::add(*q, v) : v;
+            B* q = &tb[ix[(c ? l1 : l0) + r]];
+            *q = c ? BP::add(*q, v) : v;
           } else {
-            outp[ob + r] = kind == KIND_V ? P::add(v, u[ix[r]]) : v;
+            outb[ob + r] = kind == KIND_V ? BP::add(v, bin(ix[r])) : v;
           }
         }
       }
       if (kind == KIND_V && cols == 0 && !failed) {  // all skeleton: out = u[q]
-        for (int r = tc; r < rows; r += NCT) outp[ob + r] = u[ix[r]];
+        for (int r = tc; r < rows; r += NCT) outb[ob + r] = bin(ix[r]);
       }
       // a block with rows but no columns (an empty node of a coordinate-based tree) multiplies
       // nothing: its product is zero (row IDs: block 0 sets t[p_0], block 1 adds nothing)
       if (rows > 0 && cols == 0 && !failed) {
         if (kind == KIND_S)
-          for (int r = tc; r < rows; r += NCT) outp[ob + r] = P::zero();
+          for (int r = tc; r < rows; r += NCT) outb[ob + r] = BP::zero();
         else if (kind == KIND_U && c == 0)
-          for (int r = tc; r < rows; r += NCT) t[ix[l0 + r]] = P::zero();
+          for (int r = tc; r < rows; r += NCT) tb[ix[l0 + r]] = BP::zero();
       }
       consumer_sync<NCT>();  // red is reused by the next block; t must be complete before c = 1
     }
@@ -727,9 +737,9 @@ __global__ void __launch_bounds__(RG::NTHREADS, RG::CTAS)
       if (*(volatile int*)&cons_abort) break;
       if (lev == Lv) {
         const int64_t y0 = second ? leaf_start(d1, j) : leaf_start(d, j);
-        for (int i = tc; i < tl; i += NCT) io.y[y0 + i] = t[i];
+        for (int i = tc; i < tl; i += NCT) io.y[y0 + i] = BP::v_of(tb[i]);
       } else {
-        for (int i = tc; i < tl; i += NCT) outp[i < olen0 ? obv[0] + i : obv[1] + (i - olen0)] = t[i];
+        for (int i = tc; i < tl; i += NCT) outb[i < olen0 ? obv[0] + i : obv[1] + (i - olen0)] = tb[i];
       }
     }
   }

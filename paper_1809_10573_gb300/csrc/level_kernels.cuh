@@ -202,6 +202,46 @@ struct DF64S32P : DF64P {
   __device__ static __forceinline__ vec_t zero() { return make_float2(0.f, 0.f); }
 };
 
+// Vectors between levels of the single-vector forward path. With DF set the double-float
+// policy keeps them in its own format, (re_hi, re_lo, im_hi, im_lo) floats (16 bytes, like
+// complex128), so that gathering a level's operands, adding its pass-through terms and writing its
+// outputs take no FP64 arithmetic (GB300 issues FP64 at a small fraction of the FP32 rate); only
+// level 0 converts the complex128 x and level L the complex128 y. Otherwise the boundary vectors
+// are the policy's vec_t.
+template <class P, bool DF>
+struct Bnd {
+  using b_t = typename P::vec_t;
+  __device__ static __forceinline__ b_t of_v(typename P::vec_t v) { return v; }
+  __device__ static __forceinline__ typename P::vec_t v_of(b_t b) { return b; }
+  __device__ static __forceinline__ typename P::gv_t g_of(b_t b) { return P::cvt(b); }
+  __device__ static __forceinline__ b_t of_acc(const typename P::acc_t& a) { return P::fin(a); }
+  __device__ static __forceinline__ b_t add(b_t a, b_t b) { return P::add(a, b); }
+  __device__ static __forceinline__ b_t zero() { return P::zero(); }
+};
+template <>
+struct Bnd<DF64P, true> {
+  using b_t = float4;
+  __device__ static __forceinline__ b_t of_v(double2 v) { return DF64P::cvt(v); }  // exact split
+  __device__ static __forceinline__ double2 v_of(b_t b) {  // exact: 48 bits in a double
+    return make_double2((double)b.x + (double)b.y, (double)b.z + (double)b.w);
+  }
+  __device__ static __forceinline__ float4 g_of(b_t b) { return b; }
+  // a flushed accumulator: its (hi, lo) pairs, of the value fin() rounds exactly into a double
+  __device__ static __forceinline__ b_t of_acc(const DF64P::acc_t& a) { return DF64P::part(a); }
+  __device__ static __forceinline__ b_t add(b_t a, b_t b) {
+    dw_accumulate(a.x, a.y, b.x, b.y);
+    dw_accumulate(a.z, a.w, b.z, b.w);
+    return a;
+  }
+  __device__ static __forceinline__ b_t zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+// the single-vector forward bodies of the double-float policy use its own boundary format
+template <class P, int RB, int RPT>
+constexpr bool df_boundary() {
+  return std::is_same<P, DF64P>::value && RB == 1 && RPT == 0;
+}
+static_assert(sizeof(Bnd<DF64P, true>::b_t) == sizeof(DF64P::vec_t), "boundary elements keep their size");
+
 template <class P> constexpr int fmt_of();
 template <> constexpr int fmt_of<FP64P>() { return IDBF_STORE_C128; }
 template <> constexpr int fmt_of<DF64P>() { return IDBF_STORE_DF64; }
@@ -336,10 +376,15 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
   using V = typename P::vec_t;
   using G = typename P::gv_t;
   using M = typename P::mat_t;
+  using BP = Bnd<P, df_boundary<P, RB, RPT>()>;
+  using B = typename BP::b_t;
   V* u = (V*)smem;
+  B* ub = (B*)u;  // the inputs of a level > 0, in the boundary format
   G* g = (G*)(u + (size_t)max_in * RB);
-  V* res = (V*)(g + (size_t)2 * gcap * RB);
-  V* t = (V*)g;  // phase 4 of a U level only, after the last read of g
+  B* res = (B*)(g + (size_t)2 * gcap * RB);
+  B* t = (B*)g;  // phase 4 of a U level only, after the last read of g
+  const B* winb = (const B*)io.win;
+  B* woutb = (B*)io.wout;
   const int nrb = min(RB, io.R - r0);
   const int tid = threadIdx.x, nt = blockDim.x;
 
@@ -360,9 +405,14 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
     for (int i = tid; i < (l0 + l1) * RB; i += nt) {
       const int e = i / RB, rb = i % RB;
       const int64_t off = e < l0 ? o0 + e : o1 + (e - l0);
-      u[i] = rb < nrb ? io.win[off * io.R + r0 + rb] : P::zero();
+      ub[i] = rb < nrb ? winb[off * io.R + r0 + rb] : BP::zero();
     }
   }
+  const bool lev0 = d.lev == 0;
+  // gathered operand of input element e: level 0 converts x, later levels read the boundary
+  auto gin = [&](int e) -> G { return lev0 ? P::cvt(u[e]) : BP::g_of(ub[e]); };
+  // pass-through term of input element e, in the boundary format
+  auto bin = [&](int e) -> B { return lev0 ? BP::of_v(u[e]) : ub[e]; };
   const int rows0 = d.rows[2 * j], rows1 = d.rows[2 * j + 1];
   const int cols0 = d.cols[2 * j], cols1 = d.cols[2 * j + 1];
   const int64_t mo0 = d.moff[2 * j], mo1 = d.moff[2 * j + 1];
@@ -372,12 +422,12 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
 
   // phase 2: gathered operands
   if (d.kind == KIND_V) {
-    for (int i = tid; i < cols0 * RB; i += nt) g[i] = P::cvt(u[ix0[rows0 + i / RB] * RB + i % RB]);
-    for (int i = tid; i < cols1 * RB; i += nt) g[gcap * RB + i] = P::cvt(u[ix1[rows1 + i / RB] * RB + i % RB]);
+    for (int i = tid; i < cols0 * RB; i += nt) g[i] = gin(ix0[rows0 + i / RB] * RB + i % RB);
+    for (int i = tid; i < cols1 * RB; i += nt) g[gcap * RB + i] = gin(ix1[rows1 + i / RB] * RB + i % RB);
   } else if (d.kind == KIND_S) {
-    for (int i = tid; i < (l0 + l1) * RB; i += nt) g[i] = P::cvt(u[i]);
+    for (int i = tid; i < (l0 + l1) * RB; i += nt) g[i] = gin(i);
   } else {
-    for (int i = tid; i < (l0 + l1) * RB; i += nt) g[i < l0 * RB ? i : gcap * RB + i - l0 * RB] = P::cvt(u[i]);
+    for (int i = tid; i < (l0 + l1) * RB; i += nt) g[i < l0 * RB ? i : gcap * RB + i - l0 * RB] = gin(i);
   }
   __syncthreads();
 
@@ -415,7 +465,7 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
 #pragma unroll
     for (int rb = 0; rb < RB; ++rb) {
       P::flush(acc[rb]);
-      res[(c * rcap + r) * RB + rb] = P::fin(acc[rb]);
+      res[(c * rcap + r) * RB + rb] = BP::of_acc(acc[rb]);
     }
   }
   }
@@ -430,9 +480,9 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
       const int64_t ob = d.out_off[s];
       for (int i = tid; i < rows * nrb; i += nt) {
         const int r = i / nrb, rb = i % nrb;
-        V v = res[(c * rcap + r) * RB + rb];
-        if (d.kind == KIND_V) v = P::add(v, u[q[r] * RB + rb]);
-        io.wout[(ob + r) * io.R + r0 + rb] = v;
+        B v = res[(c * rcap + r) * RB + rb];
+        if (d.kind == KIND_V) v = BP::add(v, bin(q[r] * RB + rb));
+        woutb[(ob + r) * io.R + r0 + rb] = v;
       }
     }
     return;
@@ -440,23 +490,23 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
   // row-ID level: t[q_c] += in_c, t[p_c] += res_c. q_0 and p_0 partition t, so block 0
   // initialises every position once; block 1 (q_1, p_1 also a partition) then adds.
   const int tl = l0 + rows0;  // |t| = |q_0| + |p_0|
-  for (int i = tid; i < l0 * RB; i += nt) t[ix0[i / RB] * RB + i % RB] = u[i];
+  for (int i = tid; i < l0 * RB; i += nt) t[ix0[i / RB] * RB + i % RB] = bin(i);
   for (int i = tid; i < rows0 * RB; i += nt) t[ix0[l0 + i / RB] * RB + i % RB] = res[i];
   __syncthreads();
   for (int i = tid; i < l1 * RB; i += nt) {
-    V* dst = &t[ix1[i / RB] * RB + i % RB];
-    *dst = P::add(*dst, u[l0 * RB + i]);
+    B* dst = &t[ix1[i / RB] * RB + i % RB];
+    *dst = BP::add(*dst, bin(l0 * RB + i));
   }
   for (int i = tid; i < rows1 * RB; i += nt) {
-    V* dst = &t[ix1[l1 + i / RB] * RB + i % RB];
-    *dst = P::add(*dst, res[rcap * RB + i]);
+    B* dst = &t[ix1[l1 + i / RB] * RB + i % RB];
+    *dst = BP::add(*dst, res[rcap * RB + i]);
   }
   __syncthreads();
   if (d.lev == d.L) {
     const int64_t y0 = leaf_start(d, j);
     for (int i = tid; i < tl * nrb; i += nt) {
       const int e = i / nrb, rb = i % nrb;
-      io.y[y0 + e + (int64_t)(r0 + rb) * io.ldy] = t[e * RB + rb];
+      io.y[y0 + e + (int64_t)(r0 + rb) * io.ldy] = BP::v_of(t[e * RB + rb]);
     }
   } else {
     const int64_t s0 = out_seg_id(d, j, 0), s1 = out_seg_id(d, j, 1);
@@ -465,7 +515,7 @@ __device__ __forceinline__ void fwd_node(const DevLevel& d, const typename P::ma
     for (int i = tid; i < tl * nrb; i += nt) {
       const int e = i / nrb, rb = i % nrb;
       const int64_t off = e < len0 ? b0 + e : b1 + (e - len0);
-      io.wout[off * io.R + r0 + rb] = t[e * RB + rb];
+      woutb[off * io.R + r0 + rb] = t[e * RB + rb];
     }
   }
 }
@@ -773,9 +823,14 @@ __device__ __forceinline__ void fwd_node_warp(const DevLevel& d, const typename 
   using V = typename P::vec_t;
   using G = typename P::gv_t;
   using M = typename P::mat_t;
+  using BP = Bnd<P, df_boundary<P, 1, 0>()>;
+  using B = typename BP::b_t;
   V* u = (V*)wsm;
+  B* ub = (B*)u;  // the inputs of a level > 0, in the boundary format
   G* g = (G*)(u + max_in);
-  V* t = (V*)(g + 2 * (size_t)gcap);
+  B* t = (B*)(g + 2 * (size_t)gcap);
+  const B* winb = (const B*)io.win;
+  B* woutb = (B*)io.wout;
   const int lane = threadIdx.x & 31;
 
   // inputs -> u
@@ -788,8 +843,11 @@ __device__ __forceinline__ void fwd_node_warp(const DevLevel& d, const typename 
     l0 = d.in_len[2 * j];
     l1 = d.in_len[2 * j + 1];
     const int64_t o0 = d.in_off[2 * j], o1 = d.in_off[2 * j + 1];
-    for (int e = lane; e < l0 + l1; e += 32) u[e] = io.win[(e < l0 ? o0 + e : o1 + (e - l0)) * io.R];
+    for (int e = lane; e < l0 + l1; e += 32) ub[e] = winb[(e < l0 ? o0 + e : o1 + (e - l0)) * io.R];
   }
+  const bool lev0 = d.lev == 0;
+  auto gin = [&](int e) -> G { return lev0 ? P::cvt(u[e]) : BP::g_of(ub[e]); };
+  auto bin = [&](int e) -> B { return lev0 ? BP::of_v(u[e]) : ub[e]; };
   const int rowsv[2] = {d.rows[2 * j], d.rows[2 * j + 1]};
   const int colsv[2] = {d.cols[2 * j], d.cols[2 * j + 1]};
   const int64_t mov[2] = {d.moff[2 * j], d.moff[2 * j + 1]};
@@ -800,17 +858,17 @@ __device__ __forceinline__ void fwd_node_warp(const DevLevel& d, const typename 
   if (d.kind == KIND_V) {
 #pragma unroll
     for (int c = 0; c < 2; ++c)
-      for (int k = lane; k < colsv[c]; k += 32) g[c * gcap + k] = P::cvt(u[ixv[c][rowsv[c] + k]]);
+      for (int k = lane; k < colsv[c]; k += 32) g[c * gcap + k] = gin(ixv[c][rowsv[c] + k]);
   } else if (d.kind == KIND_S) {
-    for (int e = lane; e < l0 + l1; e += 32) g[e] = P::cvt(u[e]);
+    for (int e = lane; e < l0 + l1; e += 32) g[e] = gin(e);
   } else {
-    for (int e = lane; e < l0; e += 32) g[e] = P::cvt(u[e]);
-    for (int e = lane; e < l1; e += 32) g[gcap + e] = P::cvt(u[l0 + e]);
+    for (int e = lane; e < l0; e += 32) g[e] = gin(e);
+    for (int e = lane; e < l1; e += 32) g[gcap + e] = gin(l0 + e);
   }
   __syncwarp();
 
   // block products: lane owns rows lane + 32 i
-  V res[2][RPL];
+  B res[2][RPL];
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     const int rows = rowsv[c], cols = colsv[c];
@@ -858,7 +916,7 @@ __device__ __forceinline__ void fwd_node_warp(const DevLevel& d, const typename 
       P::flush(acc0[i]);
       P::flush(acc1[i]);
       P::combine(acc0[i], P::part(acc1[i]));
-      res[c][i] = P::fin(acc0[i]);
+      res[c][i] = BP::of_acc(acc0[i]);
     }
     if (d.kind != KIND_U) {
       const int64_t ob = d.out_off[out_seg_id(d, j, c)];
@@ -866,9 +924,9 @@ __device__ __forceinline__ void fwd_node_warp(const DevLevel& d, const typename 
       for (int i = 0; i < RPL; ++i) {
         const int r = lane + 32 * i;
         if (r >= rows) continue;
-        V v = res[c][i];
-        if (d.kind == KIND_V) v = P::add(v, u[ixv[c][r]]);
-        io.wout[(ob + r) * io.R] = v;
+        B v = res[c][i];
+        if (d.kind == KIND_V) v = BP::add(v, bin(ixv[c][r]));
+        woutb[(ob + r) * io.R] = v;
       }
     }
   }
@@ -876,7 +934,7 @@ __device__ __forceinline__ void fwd_node_warp(const DevLevel& d, const typename 
   // row-ID level: t[q_c] = in_c, t[p_c] = res_c, block 0 first (q_0, p_0 partition t), then
   // block 1 adds (q_1, p_1 also a partition)
   const int tl = l0 + rowsv[0];
-  for (int e = lane; e < l0; e += 32) t[ixv[0][e]] = u[e];
+  for (int e = lane; e < l0; e += 32) t[ixv[0][e]] = bin(e);
 #pragma unroll
   for (int i = 0; i < RPL; ++i) {
     const int r = lane + 32 * i;
@@ -884,25 +942,25 @@ __device__ __forceinline__ void fwd_node_warp(const DevLevel& d, const typename 
   }
   __syncwarp();
   for (int e = lane; e < l1; e += 32) {
-    V* dst = &t[ixv[1][e]];
-    *dst = P::add(*dst, u[l0 + e]);
+    B* dst = &t[ixv[1][e]];
+    *dst = BP::add(*dst, bin(l0 + e));
   }
 #pragma unroll
   for (int i = 0; i < RPL; ++i) {
     const int r = lane + 32 * i;
     if (r < rowsv[1]) {
-      V* dst = &t[ixv[1][l1 + r]];
-      *dst = P::add(*dst, res[1][i]);
+      B* dst = &t[ixv[1][l1 + r]];
+      *dst = BP::add(*dst, res[1][i]);
     }
   }
   __syncwarp();
   if (d.lev == d.L) {
-    for (int e = lane; e < tl; e += 32) io.y[j * d.n0 + e] = t[e];
+    for (int e = lane; e < tl; e += 32) io.y[j * d.n0 + e] = BP::v_of(t[e]);
   } else {
     const int64_t s0 = out_seg_id(d, j, 0), s1 = out_seg_id(d, j, 1);
     const int len0 = d.out_len[s0];
     const int64_t b0 = d.out_off[s0], b1 = d.out_off[s1];
-    for (int e = lane; e < tl; e += 32) io.wout[(e < len0 ? b0 + e : b1 + (e - len0)) * io.R] = t[e];
+    for (int e = lane; e < tl; e += 32) woutb[(e < len0 ? b0 + e : b1 + (e - len0)) * io.R] = t[e];
   }
 }
 
